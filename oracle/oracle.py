@@ -1,0 +1,304 @@
+"""FP64 CPU oracle of the explicit FD wave solvers (arXiv 1608.03984).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers. It shares no code
+with the GPU library; the C kernels are in ``fdoracle.c`` (plain loops in
+the paper's order and notation), this module marshals numpy arrays and holds
+the set-up steps the paper states as formulas (CFL limit of Eq. stability,
+the sponge-medium extension, c = dt^2 v^2).
+
+Array convention: numpy arrays of shape (nz, ny, nx), C order, x fastest.
+Positions are (x, y, z) metres of the physical grid, whose first point is at
+the origin; the computational grid adds ``nb`` sponge points on every face.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fdoracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libfdoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.c_int
+_F = ctypes.c_double
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, -O2, OpenMP) into oracle/_build."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "fdoracle.h"))):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            sig = {
+                "or_fornberg": [_I, _D, _F, _I, _D],
+                "or_fd_weights": [_I, _D, _D],
+                "or_laplacian": [_I, _I, _I, _I, _F, _I, _D, _D],
+                "or_derivative": [_I, _I, _I, _I, _F, _I, _I, _D, _D],
+                "or_rotated": [_I, _I, _I, _I, _F, _I, _D, _D, _D, _D, _D, _D],
+                "or_sponge_profile": [_I, _I, _F, _D],
+                "or_interpolate": [_I, _I, _I, _F, _I, _D, _I, _D, _D],
+                "or_acoustic_step": [_I, _I, _I, _I, _F, _I, _I, _F, _D, _D, _D, _D, _D, _D,
+                                     _I, _D, _D, _D],
+                "or_acoustic_forward": [_I, _I, _I, _I, _F, _I, _F, _D, _D, _D, _D, _I, _D, _D,
+                                        _I, _I, _D, _D, _D, _D, _D],
+                "or_tti_step": [_I, _I, _I, _I, _F, _I, _I, _F, _D, _D, _D, _D, _D, _D, _D, _D,
+                                _D, _D, _D, _D, _I, _D, _D, _D, _D],
+                "or_tti_forward": [_I, _I, _I, _I, _F, _I, _F, _D, _D, _D, _D, _D, _D, _D, _D,
+                                   _I, _D, _D, _I, _I, _D, _D, _D],
+                "or_acoustic_adjoint": [_I, _I, _I, _I, _F, _I, _F, _D, _D, _D, _D, _I, _D, _D,
+                                        _I, _I, _D, _D, _D, _D],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = _I
+            L.or_sponge_gamma_max.argtypes = [_F, _I, _F, _F]
+            L.or_sponge_gamma_max.restype = _F
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    """double* of a C-contiguous float64 array, or NULL for None."""
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous, (a.dtype, a.flags)
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _chk(rc, what):
+    if rc != 0:
+        raise ValueError("oracle %s failed (rc=%d)" % (what, rc))
+
+
+# --------------------------------------------------------------------------
+# weights and operators (Section "Stencil operators")
+# --------------------------------------------------------------------------
+
+def fornberg(x, z, mmax):
+    """Weights[node, m] of the m-th derivative at z from nodes x (Fornberg 1988)."""
+    x = _f64(np.asarray(x))
+    out = np.zeros((x.size, mmax + 1))
+    _chk(lib().or_fornberg(x.size - 1, _p(x), float(z), mmax, _p(out)), "fornberg")
+    return out
+
+
+def fd_weights(order):
+    """(w2, c1): central 2nd/1st-derivative weights at offsets 0..r (unit spacing)."""
+    r = order // 2
+    w2 = np.zeros(r + 1)
+    c1 = np.zeros(r + 1)
+    _chk(lib().or_fd_weights(order, _p(w2), _p(c1)), "fd_weights")
+    return w2, c1
+
+
+def laplacian(u, order, h, periodic=False):
+    u = _f64(u)
+    out = np.empty_like(u)
+    nz, ny, nx = u.shape
+    _chk(lib().or_laplacian(nx, ny, nz, order, h, int(periodic), _p(u), _p(out)), "laplacian")
+    return out
+
+
+DERIVS = {"x": 0, "y": 1, "z": 2, "xx": 3, "yy": 4, "zz": 5, "xy": 6, "xz": 7, "yz": 8}
+
+
+def derivative(u, which, order, h, periodic=False):
+    u = _f64(u)
+    out = np.empty_like(u)
+    nz, ny, nx = u.shape
+    _chk(lib().or_derivative(nx, ny, nz, order, h, int(periodic), DERIVS[which], _p(u), _p(out)),
+         "derivative")
+    return out
+
+
+def rotated(u, theta, phi, order, h, periodic=False):
+    """(Gxx u, Gyy u, Gzz u) of Eq. DiffOp, theta/phi per point in radians."""
+    u = _f64(u)
+    th = _f64(np.broadcast_to(theta, u.shape))
+    ph = _f64(np.broadcast_to(phi, u.shape))
+    gx, gy, gz = np.empty_like(u), np.empty_like(u), np.empty_like(u)
+    nz, ny, nx = u.shape
+    _chk(lib().or_rotated(nx, ny, nz, order, h, int(periodic), _p(th), _p(ph), _p(u),
+                          _p(gx), _p(gy), _p(gz)), "rotated")
+    return gx, gy, gz
+
+
+# --------------------------------------------------------------------------
+# set-up: stability (Eq. stability), sponge, medium on the computational grid
+# --------------------------------------------------------------------------
+
+def laplacian_abs_weight_sum(order):
+    """a2 of Eq. stability: sum of |weights| of the 3D Laplacian stencil."""
+    w2, _ = fd_weights(order)
+    return 3.0 * (abs(w2[0]) + 2.0 * np.abs(w2[1:]).sum())
+
+
+def max_stable_dt(order, h, vmax, a1=4.0):
+    """Largest dt with vmax dt / h <= sqrt(a1/a2) (Eq. stability, CFL)."""
+    return h * np.sqrt(a1 / laplacian_abs_weight_sum(order)) / vmax
+
+
+def sponge_gamma_max(vmax, nb, h, R=1e-3):
+    return lib().or_sponge_gamma_max(float(vmax), int(nb), float(h), float(R))
+
+
+def sponge_profile(n_comp, nb, gamma_max):
+    out = np.zeros(n_comp)
+    _chk(lib().or_sponge_profile(n_comp, nb, float(gamma_max), _p(out)), "sponge_profile")
+    return out
+
+
+def extend(field, nb):
+    """Physical field -> computational grid: sponge points take the value of
+    the nearest physical point (the medium continues into the sponge)."""
+    return np.pad(np.asarray(field, dtype=np.float64), nb, mode="edge")
+
+
+class Setup:
+    """Computational-grid medium and damping for a physical model.
+
+    vp: physical velocity (nz, ny, nx) m/s; eps/delta/theta/phi optional TTI
+    fields (physical grid, radians for angles). `gamma_vmax` is the velocity
+    scale of the sponge (defaults to max vp)."""
+
+    def __init__(self, vp, h, nb, order, dt, R=1e-3, eps=None, delta=None, theta=None,
+                 phi=None, gamma_vmax=None):
+        self.h, self.nb, self.order, self.dt = float(h), int(nb), int(order), float(dt)
+        v = extend(vp, nb)
+        self.shape = v.shape
+        self.c = dt * dt * v * v
+        vmax = float(np.max(vp)) if gamma_vmax is None else float(gamma_vmax)
+        gmax = sponge_gamma_max(vmax, nb, h, R) if nb > 0 else 0.0
+        nz, ny, nx = self.shape
+        self.gx = sponge_profile(nx, nb, gmax)
+        self.gy = sponge_profile(ny, nb, gmax)
+        self.gz = sponge_profile(nz, nb, gmax)
+        self.eps = None if eps is None else extend(eps, nb)
+        self.delta = None if delta is None else extend(delta, nb)
+        self.theta = None if theta is None else extend(theta, nb)
+        self.phi = None if phi is None else extend(phi, nb)
+
+
+def _pos(xyz):
+    if xyz is None:
+        return 0, None
+    a = _f64(np.asarray(xyz).reshape(-1, 3))
+    return a.shape[0], a
+
+
+# --------------------------------------------------------------------------
+# time stepping (Algorithm 1)
+# --------------------------------------------------------------------------
+
+def interpolate(u, rec_xyz, h, nb):
+    u = _f64(u)
+    nrec, rx = _pos(rec_xyz)
+    out = np.zeros(nrec)
+    nz, ny, nx = u.shape
+    _chk(lib().or_interpolate(nx, ny, nz, h, nb, _p(u), nrec, _p(rx), _p(out)), "interpolate")
+    return out
+
+
+def acoustic_step(s: Setup, u, um, src_xyz=None, amp=None, periodic=False, damping=True):
+    u, um = _f64(u), _f64(um)
+    up = np.empty_like(u)
+    nsrc, sx = _pos(src_xyz)
+    a = _f64(np.atleast_1d(amp)) if nsrc else None
+    nz, ny, nx = u.shape
+    g = (s.gx, s.gy, s.gz) if damping else (None, None, None)
+    _chk(lib().or_acoustic_step(nx, ny, nz, s.order, s.h, int(periodic), s.nb, s.dt,
+                                _p(_f64(s.c)), _p(g[0]), _p(g[1]), _p(g[2]), _p(u), _p(um),
+                                nsrc, _p(sx), _p(a), _p(up)), "acoustic_step")
+    return up
+
+
+def acoustic_forward(s: Setup, src_xyz, wavelet, nt, rec_xyz=None, history=False):
+    """Returns dict(traces[(nt+1), nrec], u, um, history?)."""
+    nsrc, sx = _pos(src_xyz)
+    w = _f64(np.asarray(wavelet).reshape(nt, nsrc)) if nsrc else None
+    nrec, rx = _pos(rec_xyz)
+    traces = np.zeros((nt + 1, max(nrec, 0)))
+    u = np.zeros(s.shape)
+    um = np.zeros(s.shape)
+    hist = np.zeros((nt + 1,) + s.shape) if history else None
+    nz, ny, nx = s.shape
+    _chk(lib().or_acoustic_forward(nx, ny, nz, s.order, s.h, s.nb, s.dt, _p(_f64(s.c)),
+                                   _p(s.gx), _p(s.gy), _p(s.gz), nsrc, _p(sx), _p(w), nt,
+                                   nrec, _p(rx), _p(traces) if nrec else None, _p(u), _p(um),
+                                   _p(hist)), "acoustic_forward")
+    out = {"traces": traces, "u": u, "um": um}
+    if history:
+        out["history"] = hist
+    return out
+
+
+def acoustic_adjoint(s: Setup, rec_xyz, res, nt, src_xyz=None, history=None):
+    """Adjoint of acoustic_forward: returns dict(wavelet_adj[nt, nsrc], grad_m)."""
+    nrec, rx = _pos(rec_xyz)
+    res = _f64(np.asarray(res).reshape(nt + 1, nrec))
+    nsrc, sx = _pos(src_xyz)
+    wadj = np.zeros((nt, nsrc)) if nsrc else None
+    grad = np.zeros(s.shape) if history is not None else None
+    hist = _f64(history) if history is not None else None
+    nz, ny, nx = s.shape
+    _chk(lib().or_acoustic_adjoint(nx, ny, nz, s.order, s.h, s.nb, s.dt, _p(_f64(s.c)),
+                                   _p(s.gx), _p(s.gy), _p(s.gz), nrec, _p(rx), _p(res), nt,
+                                   nsrc, _p(sx), _p(wadj), _p(hist), _p(grad)),
+         "acoustic_adjoint")
+    return {"wavelet_adj": wadj, "grad_m": grad}
+
+
+def tti_step(s: Setup, p, pm, r, rm, src_xyz=None, amp=None, periodic=False, damping=True):
+    p, pm, r, rm = _f64(p), _f64(pm), _f64(r), _f64(rm)
+    pp, rp = np.empty_like(p), np.empty_like(r)
+    nsrc, sx = _pos(src_xyz)
+    a = _f64(np.atleast_1d(amp)) if nsrc else None
+    nz, ny, nx = p.shape
+    g = (s.gx, s.gy, s.gz) if damping else (None, None, None)
+    _chk(lib().or_tti_step(nx, ny, nz, s.order, s.h, int(periodic), s.nb, s.dt, _p(_f64(s.c)),
+                           _p(s.eps), _p(s.delta), _p(s.theta), _p(s.phi), _p(g[0]), _p(g[1]),
+                           _p(g[2]), _p(p), _p(pm), _p(r), _p(rm), nsrc, _p(sx), _p(a),
+                           _p(pp), _p(rp)), "tti_step")
+    return pp, rp
+
+
+def tti_forward(s: Setup, src_xyz, wavelet, nt, rec_xyz=None):
+    """Returns dict(traces, p, pm, r, rm)."""
+    nsrc, sx = _pos(src_xyz)
+    w = _f64(np.asarray(wavelet).reshape(nt, nsrc)) if nsrc else None
+    nrec, rx = _pos(rec_xyz)
+    traces = np.zeros((nt + 1, max(nrec, 0)))
+    fields = np.zeros((4,) + s.shape)
+    nz, ny, nx = s.shape
+    _chk(lib().or_tti_forward(nx, ny, nz, s.order, s.h, s.nb, s.dt, _p(_f64(s.c)), _p(s.eps),
+                              _p(s.delta), _p(s.theta), _p(s.phi), _p(s.gx), _p(s.gy), _p(s.gz),
+                              nsrc, _p(sx), _p(w), nt, nrec, _p(rx),
+                              _p(traces) if nrec else None, _p(fields)), "tti_forward")
+    return {"traces": traces, "p": fields[0], "pm": fields[1], "r": fields[2], "rm": fields[3]}
