@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Grid-point updates per second of the explicit FD wave step on GB300.
+
+Workload: the smooth-random acoustic model, 512^3 physical points, h = 10 m,
+40-point sponge on every face (592^3 computational points), Ricker 10 Hz
+source at the centre, 256 x 256 receivers at 20 m depth, dt at CFL 0.4.
+A bench step advances one time step at EACH space order 2/4/8/12/16 (five
+solvers, the order sweep), i.e. the whole hot path five times: stencil
+update with fused sponge, source injection, receiver interpolation.
+
+Outputs one JSON line (rank 0). `value` is whole-job Gpts/s (computational
+points x orders x steps / time, all ranks); the roofline entry is the
+stencil kernel's algorithmic bytes (16 B per point: read u_n, u_{n-1}, c;
+write u_{n+1}) over its CUDA-event time, against the measured HBM copy
+bandwidth. `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ORDERS = (2, 4, 8, 12, 16)
+BYTES_PER_POINT = 16          # acoustic l + s = 4 fields x 4 B (Section "Operational intensity")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="fdwave", choices=["fdwave", "reference"])
+    p.add_argument("--n", type=int, default=512, help="physical grid points per axis")
+    p.add_argument("--nb", type=int, default=40)
+    p.add_argument("--orders", default=",".join(map(str, ORDERS)))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("acoustic.cu", "ptx.cuh", "fdw_internal.h"):
+        with open(os.path.join(ROOT, "paper_1608_03984_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_point():
+    """DRAM bytes per point of the stencil kernel from the committed ncu
+    summary, if its kernel-source hash matches the current source."""
+    path = os.path.join(ROOT, "profiles", "acoustic_step_592_ncu.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"TRAFFIC_BYTES_PER_POINT\s+([0-9.]+)\s+source_sha=([0-9a-f]+)", text)
+    if not m or m.group(2) != kernel_source_sha():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(args, order, nt):
+    from paper_1608_03984_gb300 import synth
+    return synth.random_acoustic(n=args.n, nb=args.nb, order=order, nt=nt, nrec_side=256)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(vp, h, nb, order, dt, planes=16):
+    """A slab of `planes` computational z planes of the workload (full x/y
+    extent) with a smooth random state: the bounded sample the oracle steps."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1608_03984_gb300 import synth
+    k0 = vp.shape[0] // 2
+    slab = vp[k0:k0 + planes]
+    s = O.Setup(slab, h, nb, order, dt, gamma_vmax=float(vp.max()))
+    # keep the sponge in x/y only: the slab is an interior piece along z
+    s.c = s.c[nb:nb + planes]
+    s.gz = np.zeros(planes)
+    s.shape = s.c.shape
+    u = synth.random_wavefield(s.shape, 3, scale=1e-3).astype(np.float64)
+    um = synth.random_wavefield(s.shape, 4, scale=1e-3).astype(np.float64)
+    return s, u, um
+
+
+def time_oracle(samples, steps, max_seconds=None):
+    from oracle import oracle as O
+    pts = 0
+    t0 = time.perf_counter()
+    for it in range(steps):
+        for s, u, um in samples:
+            up = O.acoustic_step(s, u, um)
+            pts += up.size
+        if max_seconds and time.perf_counter() - t0 > max_seconds:
+            break
+    return pts, time.perf_counter() - t0
+
+
+def cpu_threads():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args, orders):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    from paper_1608_03984_gb300 import synth
+    base = workload(args, orders[0], 4)
+    samples = []
+    for o in orders:
+        dt = base.dt
+        samples.append(oracle_sample(base.vp, base.h, base.nb, o, dt))
+    time_oracle(samples, args.warmup)
+    pts, sec = time_oracle(samples, args.steps)
+    gpts = pts / sec / 1e9
+    nz, ny, nx = base.n_comp
+    sample_desc = ("%d x %d x %d slab (16 z planes, full x/y incl. sponge) of the 592^3 grid per order,"
+                   " orders %s, FP64 oracle" % (16, ny, nx, "/".join(map(str, orders))))
+    line = {
+        "impl": "reference", "metric": "Gpts/s per timestep", "value": gpts, "unit": "Gpts/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, orders, base),
+        "e2e": {"value": gpts, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": gpts, "unit": "Gpts/s", "cores": cpu_threads(), "kind": "oracle",
+                         "sample": sample_desc},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, orders, w):
+    nz, ny, nx = w.n_comp
+    return {"workload": "random_acoustic %d^3 + %d-point sponge (%dx%dx%d computational), h=10 m, "
+                        "orders %s (one step of each per bench step), Ricker 10 Hz, 256x256 receivers"
+                        % (args.n, args.nb, nz, ny, nx, "/".join(map(str, orders))),
+            "grid": [nz, ny, nx], "orders": list(orders), "equation": "acoustic",
+            "l2": "inputs larger than L2 (each field %.0f MB)" % (nz * ny * nx * 4 / 1e6),
+            "global_batch": len(orders), "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+def run_fdwave(args, orders):
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1608_03984_gb300 import fdwave, opmodel
+
+    nt = args.warmup + args.steps + 2
+    base = workload(args, orders[0], nt)
+    points = base.points
+    stream = torch.cuda.current_stream()
+    solvers = []
+    for o in orders:
+        s = fdwave.Solver(base.n, base.h, base.nb, o, stream=stream)
+        s.set_model(base.vp).set_dt(base.dt).set_sources(base.src_xyz, base.wavelet)
+        s.set_receivers(base.rec_xyz, nt)
+        solvers.append(s)
+
+    for s in solvers:
+        s.step(args.warmup)
+    for s in solvers:
+        s.check()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for s in solvers:
+        s.profile_begin(args.steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for s in solvers:
+            s.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kern = [s.profile_end() for s in solvers]
+    for s in solvers:
+        s.check()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    total_pts = points * len(orders) * args.steps * world
+    value = total_pts / (ms / 1e3) / 1e9
+    hbm, peak_src = peaks()
+    per_order = {}
+    sum_bytes, sum_kms = 0.0, 0.0
+    for o, (kms, nl) in zip(orders, kern):
+        k = o + 1
+        avg = kms / max(nl, 1)
+        achieved = BYTES_PER_POINT * points / (avg / 1e3) / 1e9
+        gpts_k = points / (avg / 1e3) / 1e9
+        per_order[str(o)] = {
+            "kernel_ms": avg, "kernel_gpts": gpts_k, "achieved_gbs": achieved,
+            "frac_of_measured_hbm": achieved / hbm,
+            "I_alg_paper": opmodel.oi("acoustic", k),
+            "paper_model_gflops": gpts_k * opmodel.flops_per_point("acoustic", k),
+            "roofline_gpts_paper_model": hbm / BYTES_PER_POINT,
+        }
+        sum_bytes += BYTES_PER_POINT * points * nl
+        sum_kms += kms
+    achieved = sum_bytes / (sum_kms / 1e3) / 1e9
+    tpp = ncu_traffic_per_point()
+    roof = {"kernel": "acoustic_tma_kernel (orders %s)" % "/".join(map(str, orders)),
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "peak_source": peak_src,
+            "traffic": None if tpp is None else tpp * points,
+            "algorithmic_bytes_per_launch": BYTES_PER_POINT * points}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, orders, base, stream)
+    for s in solvers:
+        s.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        samples = [oracle_sample(base.vp, base.h, base.nb, o, base.dt) for o in orders]
+        time_oracle(samples, 1)
+        pts, sec = time_oracle(samples, 10 ** 6, max_seconds=args.cpu_seconds)
+        nz, ny, nx = base.n_comp
+        cpu = {"value": pts / sec / 1e9, "unit": "Gpts/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": "16 x %d x %d slab of the %dx%dx%d grid per order (orders %s), FP64 oracle, "
+                         "%.1f s" % (ny, nx, nz, ny, nx, "/".join(map(str, orders)), sec)}
+
+    if rank == 0:
+        line = {
+            "metric": "Gpts/s per timestep", "value": value, "unit": "Gpts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_dict(args, orders, base),
+            "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, orders, base, stream):
+    """The same sweep through the public API from pinned host buffers: per
+    order, upload the model, sources, receivers, run the steps, read the
+    traces back. Host<->device copies are inside the timed region."""
+    import torch
+    from paper_1608_03984_gb300 import fdwave
+    vp_h = torch.from_numpy(base.vp).pin_memory()
+    w_h = torch.from_numpy(base.wavelet).pin_memory()
+    nsteps = args.steps
+    total = 0.0
+    h2d = d2h = 0
+    for o in orders:
+        s = fdwave.Solver(base.n, base.h, base.nb, o, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_model(vp_h).set_dt(base.dt).set_sources(base.src_xyz, w_h)
+        s.set_receivers(base.rec_xyz, nsteps)
+        s.step(nsteps)
+        tr = s.traces()
+        total += time.perf_counter() - t0
+        h2d += vp_h.numel() * 4 + w_h.numel() * 4 + base.src_xyz.nbytes + base.rec_xyz.nbytes
+        d2h += tr.nbytes
+        s.close()
+    pts = base.points * len(orders) * nsteps
+    return {"value": pts / total / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": h2d // nsteps,
+            "d2h_bytes_per_step": d2h // nsteps,
+            "note": "per order: model/sources/receivers uploaded from pinned host memory, "
+                    "%d steps, traces read back; wall clock" % nsteps}
+
+
+def main():
+    args = parse()
+    orders = tuple(int(x) for x in args.orders.split(","))
+    if args.impl == "reference":
+        run_reference(args, orders)
+    else:
+        run_fdwave(args, orders)
+
+
+if __name__ == "__main__":
+    main()

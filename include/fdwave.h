@@ -1,0 +1,200 @@
+/*
+ * fdwave.h -- C ABI of the GB300 (sm_103a) explicit finite-difference wave
+ * solver: the time-stepping hot path analysed in Louboutin et al.,
+ * "Performance prediction of finite-difference solvers for different
+ * computer architectures" (arXiv 1608.03984).
+ *
+ * What one step computes (Algorithm 1 "Time-stepping", Eq. Acou / Eq. TTI):
+ *   acoustic:  P u+ = 2u - Q u- + c (lap u + q)
+ *   TTI:       P p+ = 2p - Q p- + c [(1+2e)(Gxx+Gyy) p + sqrt(1+2d) Gzz r + q]
+ *              P r+ = 2r - Q r- + c [sqrt(1+2d)(Gxx+Gyy) p + Gzz r + q]
+ * with c = dt^2 v^2, the rotated operators of Eq. DiffOp, space order 2..16
+ * star stencils (Section "Stencil operators"), P, Q = 1 +- gamma dt/2 the
+ * linear sponge (the paper leaves boundaries out; this is the library's
+ * choice, fused in the update), q the trilinear point sources divided by
+ * h^3 ("Add Source" of Algorithm 1), followed by trilinear receiver
+ * interpolation of the new level into FP64 traces.
+ *
+ * Grids. The caller gives the PHYSICAL grid nx*ny*nz (x fastest, z depth)
+ * and spacing h in metres; the library adds nb sponge points on every face
+ * (computational grid (nx+2nb)*(ny+2nb)*(nz+2nb)). Outside the
+ * computational grid the wavefield is zero. Positions are (x, y, z) metres
+ * with the first physical point at the origin; they may lie anywhere in the
+ * computational grid, sponge included (else FDW_ERR_OUT_OF_DOMAIN).
+ *
+ * Memory and streams. Every call is ordered on the CUDA stream given at
+ * creation (NULL = the legacy default stream). The library owns its device
+ * buffers (allocated with cudaMalloc in fdw_create / fdw_set_* and freed in
+ * fdw_destroy). Pointer arguments are caller-owned and only read or written
+ * during the call; `ptr_is_device` says whether they are device pointers
+ * (copied stream-ordered) or host pointers (the call synchronises the
+ * stream before it returns). Calls on one solver are not thread-safe.
+ *
+ * Errors. Every int-returning call returns FDW_OK (0) or a negative
+ * FDW_ERR_* code and leaves a message for fdw_last_error() (thread-local).
+ * Device-side failures (a bounded wait in a kernel that gave up, a
+ * non-finite wavefield found by fdw_check) are reported by the next
+ * synchronising call. No C++ exception crosses this interface.
+ */
+#ifndef FDWAVE_H
+#define FDWAVE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDW_OK 0
+#define FDW_ERR_INVALID_ARG (-1)
+#define FDW_ERR_UNSTABLE_DT (-2)
+#define FDW_ERR_OOM (-3)
+#define FDW_ERR_CUDA (-4)
+#define FDW_ERR_STATE (-5)         /* call out of order (e.g. step before set_dt) */
+#define FDW_ERR_DIVERGED (-6)      /* non-finite wavefield */
+#define FDW_ERR_OUT_OF_DOMAIN (-7) /* source/receiver outside the grid */
+#define FDW_ERR_DEVICE_TIMEOUT (-8) /* a kernel's bounded wait gave up */
+
+typedef struct fdw_solver fdw_solver;
+
+/* equation */
+#define FDW_ACOUSTIC 0 /* Eq. Acou */
+#define FDW_TTI 1      /* Eq. TTI with Eq. DiffOp (VTI is theta = phi = 0) */
+
+/* storage type of wavefields and medium parameters; arithmetic is FP32 */
+#define FDW_F32 0
+#define FDW_BF16 1
+#define FDW_F16 2
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *fdw_last_error(void);
+
+/* Library version string. */
+const char *fdw_version(void);
+
+/*
+ * Create a solver. space_order: even, 2..16 (stencil width k = order+1,
+ * Section "Stencil operators"). nb >= 0 sponge points per face. stream: a
+ * cudaStream_t or NULL. Allocates the wavefield and medium buffers on the
+ * current CUDA device. *out receives the handle.
+ * Errors: INVALID_ARG (sizes, order, equation, storage), OOM, CUDA.
+ */
+int fdw_create(fdw_solver **out, int nx, int ny, int nz, double h, int nb, int equation,
+               int space_order, int storage, void *stream);
+
+/* Free every buffer of the solver (synchronises its stream). NULL is a no-op. */
+int fdw_destroy(fdw_solver *s);
+
+/*
+ * Set the medium from PHYSICAL-grid arrays [nz][ny][nx] float32: vp in m/s
+ * (> 0); for TTI also eps, delta (Thomsen parameters, eps >= delta >= 0
+ * recommended for stability), theta (tilt) and phi (azimuth) in radians;
+ * pass NULL for those with the acoustic equation. The sponge points take
+ * the value of the nearest physical point. Invalidates dt (call
+ * fdw_set_dt again). Errors: INVALID_ARG (NULL vp, vp <= 0 or non-finite
+ * found on a host array), CUDA.
+ */
+int fdw_set_model(fdw_solver *s, const float *vp, const float *eps, const float *delta,
+                  const float *theta, const float *phi, int ptr_is_device);
+
+/*
+ * Largest stable time step of Eq. stability (CFL): vmax dt / h <= sqrt(4/a2),
+ * a2 the sum of |weights| of the 3D Laplacian stencil; for TTI vmax is the
+ * largest vp sqrt(1+2 eps). Returns a negative value before fdw_set_model.
+ */
+double fdw_max_stable_dt(const fdw_solver *s);
+
+/*
+ * Set dt (seconds): computes c = dt^2 v^2 and the sponge damping.
+ * Errors: UNSTABLE_DT if dt > fdw_max_stable_dt, STATE before set_model.
+ */
+int fdw_set_dt(fdw_solver *s, double dt);
+
+/*
+ * Point sources: xyz [nsrc][3] metres (host), wavelet [nt][nsrc] float32
+ * (amplitude at t_n = n dt; step n injects row n, steps n >= nt inject
+ * nothing). nsrc = 0 clears the sources. Errors: INVALID_ARG, OUT_OF_DOMAIN.
+ */
+int fdw_set_sources(fdw_solver *s, int nsrc, const double *xyz, const float *wavelet, int nt,
+                    int ptr_is_device);
+
+/*
+ * Receivers: xyz [nrec][3] metres (host); traces of nt+1 rows are kept on
+ * the device in FP64, row n = interpolation of level n (row 0 of a fresh
+ * run is 0). For TTI the receivers record p. Clears the traces.
+ */
+int fdw_set_receivers(fdw_solver *s, int nrec, const double *xyz, int nt);
+
+/* Zero the wavefields, the traces and the step counter (fresh run). */
+int fdw_reset(fdw_solver *s);
+
+/* Current step index n (the state holds levels n and n-1). */
+int fdw_current_step(const fdw_solver *s);
+
+/*
+ * Advance nsteps steps (asynchronous on the stream): stencil update with
+ * fused sponge, source injection, receiver interpolation, per step.
+ * Errors: STATE (no dt), INVALID_ARG (nsteps < 0), CUDA.
+ */
+int fdw_step(fdw_solver *s, int nsteps);
+
+/*
+ * Copy the traces [(nt+1)][nrec] FP64 into out (host or device).
+ * Synchronises when out is a host pointer; reports device timeouts.
+ */
+int fdw_gather_receivers(fdw_solver *s, double *out, int ptr_is_device);
+
+/*
+ * Copy one wavefield level of the computational grid, as float32
+ * [(nz+2nb)][(ny+2nb)][(nx+2nb)], into out (host or device).
+ * field: 0 = u (acoustic) / p (TTI), 1 = r (TTI); level: 0 = n, 1 = n-1.
+ */
+int fdw_get_wavefield(const fdw_solver *s, int field, int level, float *out, int ptr_is_device);
+
+/*
+ * Overwrite one wavefield level (same layout as fdw_get_wavefield); values
+ * are rounded to the storage type. Used for checkpoints and one-step checks.
+ */
+int fdw_set_wavefield(fdw_solver *s, int field, int level, const float *in, int ptr_is_device);
+
+/* Set the step counter n (after restoring wavefields with fdw_set_wavefield). */
+int fdw_set_current_step(fdw_solver *s, int n);
+
+/*
+ * Synchronise the stream, report a device timeout flag, and when
+ * check_finite is non-zero scan the current levels for NaN/Inf
+ * (FDW_ERR_DIVERGED).
+ */
+int fdw_check(fdw_solver *s, int check_finite);
+
+/*
+ * Kernel variant of the stencil update: 0 = the 2.5D z-marching TMA
+ * kernel (default), 1 = a one-thread-per-point kernel computing the same
+ * step from plain global loads (an independent GPU formulation kept for
+ * cross-checks). Errors: INVALID_ARG.
+ */
+int fdw_set_kernel_variant(fdw_solver *s, int variant);
+
+/*
+ * Number of CTAs along z of the 2.5D kernel (each marches nz_comp/zchunks
+ * planes); 0 restores the default chosen from the grid size. fdw_get_zchunks
+ * returns the value in use (-1 for NULL).
+ */
+int fdw_set_zchunks(fdw_solver *s, int zchunks);
+int fdw_get_zchunks(const fdw_solver *s);
+
+/*
+ * Kernel timing. After fdw_profile_begin, up to max_launches (<= 65536)
+ * stencil launches issued by fdw_step are bracketed by CUDA events recorded
+ * on the solver's stream (steps are then launched individually instead of
+ * as CUDA graphs). fdw_profile_end synchronises the stream and returns the
+ * summed device time of those launches in milliseconds and their count.
+ * Errors: INVALID_ARG, STATE (end without begin), CUDA.
+ */
+int fdw_profile_begin(fdw_solver *s, int max_launches);
+int fdw_profile_end(fdw_solver *s, double *stencil_ms, int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDWAVE_H */

@@ -302,3 +302,27 @@ def tti_forward(s: Setup, src_xyz, wavelet, nt, rec_xyz=None):
                               nsrc, _p(sx), _p(w), nt, nrec, _p(rx),
                               _p(traces) if nrec else None, _p(fields)), "tti_forward")
     return {"traces": traces, "p": fields[0], "pm": fields[1], "r": fields[2], "rm": fields[3]}
+
+
+class _BlockSetup:
+    """Medium of a small block: constant c, damping given per axis."""
+
+    def __init__(self, shape, h, nb, order, dt, c, gx, gy, gz):
+        self.shape, self.h, self.nb, self.order, self.dt = shape, h, nb, order, dt
+        self.c = np.full(shape, c)
+        self.gx, self.gy, self.gz = gx, gy, gz
+
+
+def acoustic_update_at(u_block, um_c, v_c, gamma_c, h, order, dt):
+    """u_{n+1} at the centre of a (2r+1)^3 block of u_n (no source): the
+    oracle step run on the block, whose centre stencil stays inside it.
+    v_c, um_c, gamma_c: velocity, u_{n-1} and damping gamma at the centre."""
+    r = order // 2
+    n = 2 * r + 1
+    assert u_block.shape == (n, n, n)
+    gx = np.full(n, float(gamma_c))
+    z = np.zeros(n)
+    s = _BlockSetup((n, n, n), h, 0, order, dt, dt * dt * float(v_c) ** 2, gx, z, z)
+    um = np.zeros((n, n, n))
+    um[r, r, r] = um_c
+    return acoustic_step(s, u_block, um)[r, r, r]

@@ -1,0 +1,153 @@
+// fdw_internal.h -- types shared by the translation units of libfdwave
+// (sm_103a). Not part of the public C ABI (include/fdwave.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace fdw {
+
+constexpr int kMaxR = 8;          // space order 16
+constexpr int kTileX = 32;        // x extent of a stencil tile (one warp)
+
+// Device error flags (bit mask written with atomicOr).
+constexpr int kErrWaitTimeout = 1;  // an mbarrier wait gave up
+constexpr int kErrBadLaunch = 2;    // a kernel saw inconsistent launch arguments
+
+// Padded storage of one computational-grid field: x rows of Xp elements
+// (Xp a multiple of 32, so every tile row is a full 128-byte line in FP32),
+// NY rows per plane, NZ planes. Elements x in [NX, Xp) are padding and read
+// as zero through the tensor maps (their extent is NX).
+struct Dims {
+  int NX, NY, NZ;
+  int Xp;
+  __host__ __device__ size_t plane() const { return (size_t)Xp * (size_t)NY; }
+  __host__ __device__ size_t vol() const { return plane() * (size_t)NZ; }
+};
+
+// Central finite-difference weights at unit spacing, offsets 0..r.
+struct Weights {
+  float w2[kMaxR + 1];  // second derivative
+  float c1[kMaxR + 1];  // first derivative (c1[0] = 0)
+};
+
+// Damping tables: gh_a[i] = gamma_a(i) * dt / 2 for each axis.
+struct Sponge {
+  const float *gx, *gy, *gz;
+};
+
+// Storage-type traits: FP32 arithmetic on every storage type.
+template <typename T> struct St;
+template <> struct St<float> {
+  static __device__ __forceinline__ float ld(float v) { return v; }
+  static __device__ __forceinline__ float st(float v) { return v; }
+  static constexpr CUtensorMapDataType tma = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+};
+template <> struct St<__nv_bfloat16> {
+  static __device__ __forceinline__ float ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+  static __device__ __forceinline__ __nv_bfloat16 st(float v) { return __float2bfloat16_rn(v); }
+  static constexpr CUtensorMapDataType tma = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+};
+template <> struct St<__half> {
+  static __device__ __forceinline__ float ld(__half v) { return __half2float(v); }
+  static __device__ __forceinline__ __half st(float v) { return __float2half_rn(v); }
+  static constexpr CUtensorMapDataType tma = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+};
+
+// Host-side launchers (defined in the kernel translation units). Each
+// returns a cudaError_t of the launch.
+
+// Acoustic step (Eq. Acou + sponge): reads cur (level n), prev (n-1) and
+// coefficient c (= (v dt / h)^2), writes level n+1 into prev's storage.
+struct AcousticLaunch {
+  int storage;            // FDW_F32 / FDW_BF16 / FDW_F16
+  int r;                  // stencil radius (order / 2)
+  Dims d;
+  Weights w;
+  Sponge sp;
+  void *cur, *prev;       // fields (element type = storage)
+  const void *c;          // coefficient (storage type)
+  const CUtensorMap *map_cur_halo, *map_cur_int, *map_prev_int, *map_c_int;
+  int zchunks;            // CTAs along z
+  int *err;               // device error flags
+  int naive;              // 1 = one-thread-per-point kernel (debug cross-check)
+  int prepare_only;       // 1 = only set kernel attributes (outside graph capture)
+};
+cudaError_t launch_acoustic(const AcousticLaunch &L, cudaStream_t st);
+cudaError_t acoustic_prepare(int storage, int r);
+
+// Tile geometry of the 2.5D acoustic kernel for radius r and storage type,
+// used by the host to build the tensor maps.
+void acoustic_tile(int storage, int r, int *box_halo_x, int *box_halo_y, int *box_int_x,
+                   int *box_int_y);
+
+// TTI step (Eq. TTI / Eq. DiffOp + sponge).
+struct TTILaunch {
+  int storage;
+  int r;
+  Dims d;
+  Weights w;
+  Sponge sp;
+  void *p_cur, *p_prev, *r_cur, *r_prev;
+  const void *c;      // (v dt / h)^2
+  const void *e;      // 1 + 2 eps
+  const void *dl;     // sqrt(1 + 2 delta)
+  const void *ax, *ay;  // symmetry axis x/y components (sin t cos f, sin t sin f); the
+                        // z component is sqrt(1 - ax^2 - ay^2) (the operator depends on
+                        // n n^T only, so the sign of n is free)
+  int zchunks;
+  int *err;
+  int naive;
+  int prepare_only;
+};
+cudaError_t launch_tti(const TTILaunch &L, cudaStream_t st);
+cudaError_t tti_prepare(int storage, int r);
+
+// Sparse work of one step (after the stencil update):
+//   inject: u+ += c w_corner amp / (h P) at each source corner (both p and r
+//   for TTI); advances the device step counter.
+//   gather: trace[n+1][rec] = sum_corner w u+(corner) in FP64.
+struct SparseLaunch {
+  int storage;
+  Dims d;
+  Sponge sp;
+  void *f0, *f1;             // field(s) at the new level (f1 = r for TTI or null)
+  const void *c;
+  int nsrc;
+  const int *src_corner;     // [nsrc*8*3] computational (i, j, k) of each corner
+  const float *src_w;        // [nsrc*8] trilinear weight / h, 0 for dropped corners
+  const float *wavelet;      // [nt_src][nsrc]
+  int nt_src;
+  int nrec;
+  const int *rec_corner;
+  const float *rec_w;
+  double *traces;            // [(nt_rec+1)][nrec]
+  int nt_rec;
+  int *step;                 // device step counter n (of the level before the update)
+  // adjoint mode: the residual row of the level being produced is spread
+  // with receiver weights (no 1/h) -- see adjoint entry points
+  const double *residual;    // [(nt_res+1)][nrec] or null
+  int nt_res;
+  float res_scale;           // h^2: c' = c / h^2 is stored, the adjoint source is c R^T res
+  int adjoint;
+};
+cudaError_t launch_sparse(const SparseLaunch &L, cudaStream_t st);
+
+// Utility kernels (setup.cu)
+cudaError_t launch_coef_acoustic(int storage, const float *vp_phys, int nx, int ny, int nz,
+                                 int nb, Dims d, double dt_over_h, void *c, cudaStream_t st);
+cudaError_t launch_coef_tti(int storage, const float *vp, const float *eps, const float *delta,
+                            const float *theta, const float *phi, int nx, int ny, int nz,
+                            int nb, Dims d, double dt_over_h, void *c, void *e, void *dl,
+                            void *ax, void *ay, cudaStream_t st);
+cudaError_t launch_max_velocity(const float *vp, const float *eps, long n, float *out3,
+                                cudaStream_t st);
+cudaError_t launch_pack(int storage, const float *src, void *dst, Dims d,
+                        cudaStream_t st);   // dense [NZ][NY][NX] f32 -> padded storage
+cudaError_t launch_unpack(int storage, const void *src, Dims d, float *dst, cudaStream_t st);
+cudaError_t launch_nonfinite(int storage, const void *f, Dims d, int *flag, cudaStream_t st);
+
+}  // namespace fdw

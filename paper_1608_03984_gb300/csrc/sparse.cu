@@ -1,0 +1,112 @@
+// sparse.cu -- per-step sparse work after the stencil update:
+//   * source injection ("Add Source" of Algorithm 1): each point source is a
+//     discrete delta, trilinear weight / h^3, scaled like the stencil term,
+//     u+ += c w amp / (h^3 P) with c = dt^2 v^2. With the stored coefficient
+//     c' = (v dt / h)^2 this is c' w amp / (h P);
+//   * receiver interpolation: trace[n+1][rec] = sum_corner w u+(corner),
+//     FP32 values, FP64 products, sum and storage.
+// The injection kernel is also the step counter: it reads n, publishes n+1.
+#include "fdw_internal.h"
+#include "fdwave.h"
+
+namespace fdw {
+
+template <typename T> __device__ __forceinline__ void atomic_add_st(T *p, float v);
+template <> __device__ __forceinline__ void atomic_add_st<float>(float *p, float v) {
+  atomicAdd(p, v);
+}
+template <> __device__ __forceinline__ void atomic_add_st<__nv_bfloat16>(__nv_bfloat16 *p, float v) {
+  atomicAdd(p, __float2bfloat16_rn(v));
+}
+template <> __device__ __forceinline__ void atomic_add_st<__half>(__half *p, float v) {
+  atomicAdd(p, __float2half_rn(v));
+}
+
+// Corner layout shared by sources and receivers: for point s and corner q,
+// ijk[(s*8+q)*3 + a] are the computational-grid indices (always inside the
+// grid; dropped corners have weight 0).
+template <typename T>
+__global__ void __launch_bounds__(256) inject_kernel(SparseLaunch L) {
+  __shared__ int sn;
+  if (threadIdx.x == 0) sn = *L.step;
+  __syncthreads();
+  const int n = sn;
+  if (threadIdx.x == 0) *L.step = L.adjoint ? n - 1 : n + 1;
+  const size_t plane = L.d.plane();
+  if (!L.adjoint) {
+    if (n < 0 || n >= L.nt_src) return;
+    for (int t = threadIdx.x; t < L.nsrc * 8; t += blockDim.x) {
+      const float wt = L.src_w[t];
+      if (wt == 0.f) continue;
+      const int s = t >> 3;
+      const int i = L.src_corner[t * 3 + 0], j = L.src_corner[t * 3 + 1], k = L.src_corner[t * 3 + 2];
+      const size_t p = (size_t)k * plane + (size_t)j * L.d.Xp + i;
+      const float amp = L.wavelet[(size_t)n * L.nsrc + s];
+      const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[k];
+      const float cc = St<T>::ld(((const T *)L.c)[p]);
+      const float v = cc * wt * amp * __frcp_rn(1.f + gh);
+      atomic_add_st<T>((T *)L.f0 + p, v);
+      if (L.f1) atomic_add_st<T>((T *)L.f1 + p, v);
+    }
+  } else {
+    // Adjoint step producing level k = n - 1: spread residual row k with the
+    // receiver weights (no 1/h^3), scaled like the stencil term:
+    // dt^2 v^2 w res / P = c' h^2 w res / P.
+    const int k = n - 1;
+    if (k < 0 || k > L.nt_res || !L.residual) return;
+    for (int t = threadIdx.x; t < L.nrec * 8; t += blockDim.x) {
+      const float wt = L.rec_w[t];
+      if (wt == 0.f) continue;
+      const int s = t >> 3;
+      const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], kk = L.rec_corner[t * 3 + 2];
+      const size_t p = (size_t)kk * plane + (size_t)j * L.d.Xp + i;
+      const float res = (float)L.residual[(size_t)k * L.nrec + s];
+      const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[kk];
+      const float cc = St<T>::ld(((const T *)L.c)[p]);
+      atomic_add_st<T>((T *)L.f0 + p, cc * L.res_scale * wt * res * __frcp_rn(1.f + gh));
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gather_kernel(SparseLaunch L) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= L.nrec) return;
+  const int n1 = *L.step;  // level just produced
+  if (n1 < 0 || n1 > L.nt_rec) return;
+  const size_t plane = L.d.plane();
+  const T *f = (const T *)L.f0;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int t = r * 8 + q;
+    const float wt = L.rec_w[t];
+    const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], k = L.rec_corner[t * 3 + 2];
+    const float v = St<T>::ld(f[(size_t)k * plane + (size_t)j * L.d.Xp + i]);
+    acc += (double)wt * (double)v;
+  }
+  L.traces[(size_t)n1 * L.nrec + r] = acc;
+}
+
+template <typename T>
+static cudaError_t launch_sparse_t(const SparseLaunch &L, cudaStream_t st) {
+  inject_kernel<T><<<1, 256, 0, st>>>(L);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (!L.adjoint && L.nrec > 0 && L.traces) {
+    gather_kernel<T><<<(L.nrec + 255) / 256, 256, 0, st>>>(L);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+cudaError_t launch_sparse(const SparseLaunch &L, cudaStream_t st) {
+  switch (L.storage) {
+    case FDW_F32: return launch_sparse_t<float>(L, st);
+    case FDW_BF16: return launch_sparse_t<__nv_bfloat16>(L, st);
+    case FDW_F16: return launch_sparse_t<__half>(L, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fdw

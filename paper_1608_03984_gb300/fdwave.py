@@ -1,0 +1,272 @@
+"""ctypes binding of libfdwave (include/fdwave.h): argument marshalling only.
+
+Every compute step runs in the CUDA library; this module converts numpy
+arrays / torch tensors into pointers and checks return codes. Importing it
+does not load the library; the first call does, and fails loudly when the
+library has not been built (``python -c "import __graft_entry__ as g;
+g.build()"``) -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+FDW_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "UNSTABLE_DT", -3: "OOM", -4: "CUDA", -5: "STATE",
+          -6: "DIVERGED", -7: "OUT_OF_DOMAIN", -8: "DEVICE_TIMEOUT"}
+ACOUSTIC, TTI = 0, 1
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+EQUATION = {"acoustic": ACOUSTIC, "tti": TTI}
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGS = {
+    "fdw_last_error": ([], ctypes.c_char_p),
+    "fdw_version": ([], ctypes.c_char_p),
+    "fdw_create": ([ctypes.POINTER(_P), _I, _I, _I, _D, _I, _I, _I, _I, _P], _I),
+    "fdw_destroy": ([_P], _I),
+    "fdw_set_model": ([_P, _P, _P, _P, _P, _P, _I], _I),
+    "fdw_max_stable_dt": ([_P], _D),
+    "fdw_set_dt": ([_P, _D], _I),
+    "fdw_set_sources": ([_P, _I, _P, _P, _I, _I], _I),
+    "fdw_set_receivers": ([_P, _I, _P, _I], _I),
+    "fdw_reset": ([_P], _I),
+    "fdw_current_step": ([_P], _I),
+    "fdw_set_current_step": ([_P, _I], _I),
+    "fdw_step": ([_P, _I], _I),
+    "fdw_gather_receivers": ([_P, _P, _I], _I),
+    "fdw_get_wavefield": ([_P, _I, _I, _P, _I], _I),
+    "fdw_set_wavefield": ([_P, _I, _I, _P, _I], _I),
+    "fdw_check": ([_P, _I], _I),
+    "fdw_set_kernel_variant": ([_P, _I], _I),
+    "fdw_set_zchunks": ([_P, _I], _I),
+    "fdw_get_zchunks": ([_P], _I),
+    "fdw_profile_begin": ([_P, _I], _I),
+    "fdw_profile_end": ([_P, ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
+}
+
+
+class FdwError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fdwave error %d (%s): %s" % (code, ERRORS.get(code, "?"), msg))
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def lib(build_if_missing: bool = False):
+    """Load libfdwave.so (raises if it is missing: no fallback path exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError("libfdwave.so is not built (%s); run "
+                                       "`python -c \"import __graft_entry__ as g; g.build()\"`"
+                                       % path)
+                _build.build()
+            L = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def declared_symbols(header: str | None = None):
+    """Names of the functions declared in include/fdwave.h."""
+    header = header or os.path.join(_build.INCLUDE, "fdwave.h")
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdw_\w+)\s*\(", text)))
+
+
+def _chk(rc):
+    if rc != FDW_OK:
+        raise FdwError(rc, lib().fdw_last_error().decode())
+    return rc
+
+
+def _is_torch(a):
+    return type(a).__module__.split(".")[0] == "torch"
+
+
+def _ptr(a, dtype):
+    """(pointer, is_device, keepalive) for a numpy array or torch tensor."""
+    if a is None:
+        return None, 0, None
+    if _is_torch(a):
+        import torch
+        tdt = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+        t = a.detach().contiguous()
+        if t.dtype != tdt:
+            t = t.to(tdt)
+        return t.data_ptr(), int(t.is_cuda), t
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, 0, arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Solver:
+    """One wave-equation solver on the current CUDA device.
+
+    shape: physical grid (nz, ny, nx); h metres; nb sponge points per face;
+    order: space order 2..16; equation: "acoustic" | "tti";
+    storage: "f32" | "bf16" | "f16". Stream: torch stream / raw handle /
+    None (torch's current stream)."""
+
+    def __init__(self, shape, h, nb, order, equation="acoustic", storage="f32", stream=None):
+        self.shape = tuple(int(n) for n in shape)
+        self.h, self.nb, self.order = float(h), int(nb), int(order)
+        self.equation, self.storage = equation, storage
+        nz, ny, nx = self.shape
+        self.comp_shape = (nz + 2 * nb, ny + 2 * nb, nx + 2 * nb)
+        self.stream = _stream_handle(stream)
+        handle = _P()
+        _chk(lib().fdw_create(ctypes.byref(handle), nx, ny, nz, self.h, self.nb,
+                              EQUATION[equation], self.order, STORAGE[storage], self.stream))
+        self._h = handle
+        self.nrec = 0
+        self.nt_rec = 0
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fdw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- set-up -----------------------------------------------------------
+    def set_model(self, vp, eps=None, delta=None, theta=None, phi=None):
+        ptrs = [_ptr(a, np.float32) for a in (vp, eps, delta, theta, phi)]
+        dev = ptrs[0][1]
+        if any(p[0] is not None and p[1] != dev for p in ptrs):
+            raise ValueError("model arrays must all be host or all device")
+        _chk(lib().fdw_set_model(self._h, *[p[0] for p in ptrs], dev))
+        return self
+
+    def max_stable_dt(self):
+        return lib().fdw_max_stable_dt(self._h)
+
+    def set_dt(self, dt):
+        _chk(lib().fdw_set_dt(self._h, float(dt)))
+        self.dt = float(dt)
+        return self
+
+    def set_sources(self, xyz, wavelet):
+        xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+        nsrc = xyz.shape[0]
+        if nsrc == 0:
+            _chk(lib().fdw_set_sources(self._h, 0, None, None, 0, 0))
+            return self
+        wp, dev, keep = _ptr(wavelet, np.float32)
+        nt = (keep.numel() if _is_torch(keep) else keep.size) // nsrc
+        _chk(lib().fdw_set_sources(self._h, nsrc, xyz.ctypes.data, wp, nt, dev))
+        return self
+
+    def set_receivers(self, xyz, nt):
+        xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+        _chk(lib().fdw_set_receivers(self._h, xyz.shape[0], xyz.ctypes.data if xyz.size else None,
+                                     int(nt)))
+        self.nrec, self.nt_rec = xyz.shape[0], int(nt)
+        return self
+
+    # -- time loop --------------------------------------------------------
+    def reset(self):
+        _chk(lib().fdw_reset(self._h))
+        return self
+
+    @property
+    def current_step(self):
+        return lib().fdw_current_step(self._h)
+
+    def set_current_step(self, n):
+        _chk(lib().fdw_set_current_step(self._h, int(n)))
+
+    def step(self, n=1):
+        _chk(lib().fdw_step(self._h, int(n)))
+        return self
+
+    def check(self, finite=True):
+        _chk(lib().fdw_check(self._h, int(finite)))
+
+    # -- outputs / state ---------------------------------------------------
+    def traces(self, out=None):
+        """Receiver traces [(nt+1), nrec] float64 (numpy, or into a torch tensor)."""
+        if out is None:
+            out = np.zeros((self.nt_rec + 1, self.nrec), dtype=np.float64)
+        p, dev, keep = _ptr(out, np.float64)
+        _chk(lib().fdw_gather_receivers(self._h, p, dev))
+        return keep if not _is_torch(out) or keep is out else out.copy_(keep)
+
+    def wavefield(self, field=0, level=0, out=None):
+        """Computational-grid field level as float32 (numpy, or into a torch tensor)."""
+        if out is None:
+            out = np.zeros(self.comp_shape, dtype=np.float32)
+        p, dev, keep = _ptr(out, np.float32)
+        _chk(lib().fdw_get_wavefield(self._h, int(field), int(level), p, dev))
+        return keep if not _is_torch(out) or keep is out else out.copy_(keep)
+
+    def set_wavefield(self, data, field=0, level=0):
+        p, dev, keep = _ptr(data, np.float32)
+        _chk(lib().fdw_set_wavefield(self._h, int(field), int(level), p, dev))
+
+    # -- tuning / cross-checks ---------------------------------------------
+    def set_kernel_variant(self, variant):
+        """0 = 2.5D TMA kernel (default), 1 = one-thread-per-point kernel."""
+        _chk(lib().fdw_set_kernel_variant(self._h, int(variant)))
+
+    def set_zchunks(self, zchunks):
+        _chk(lib().fdw_set_zchunks(self._h, int(zchunks)))
+
+    @property
+    def zchunks(self):
+        return lib().fdw_get_zchunks(self._h)
+
+    def profile_begin(self, max_launches=65536):
+        _chk(lib().fdw_profile_begin(self._h, int(max_launches)))
+
+    def profile_end(self):
+        """(summed stencil-kernel milliseconds, number of launches timed)."""
+        ms, n = _D(), _I()
+        _chk(lib().fdw_profile_end(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value

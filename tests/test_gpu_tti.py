@@ -1,0 +1,89 @@
+"""GPU parity of the TTI step (Eq. TTI with Eq. DiffOp and the sponge)
+against the FP64 oracle, through the C ABI. Same tolerances as acoustic."""
+import numpy as np
+import pytest
+
+from paper_1608_03984_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+STEP_TOL = 1e-5
+RUN_TOL = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def tti_solver(fdw, w, storage="f32"):
+    s = fdw.Solver(w.n, w.h, w.nb, w.order, equation="tti", storage=storage)
+    s.set_model(w.vp, w.eps, w.delta, w.theta, w.phi).set_dt(w.dt)
+    s.set_sources(w.src_xyz, w.wavelet).set_receivers(w.rec_xyz, w.nt)
+    return s
+
+
+def tti_setup(O, w):
+    return O.Setup(w.vp, w.h, w.nb, w.order, w.dt, eps=w.eps, delta=w.delta, theta=w.theta,
+                   phi=w.phi)
+
+
+def small_tti(n=(26, 21, 35), order=8, nt=12, seed=None):
+    w = synth.random_tti(n=max(n), nb=5, order=order, nt=nt, nrec_side=5, seed=seed)
+    nz, ny, nx = n
+    for f in ("vp", "eps", "delta", "theta", "phi"):
+        setattr(w, f, np.ascontiguousarray(getattr(w, f)[:nz, :ny, :nx]))
+    w.n = n
+    w.src_xyz = np.array([[(nx - 1) * w.h * 0.4, (ny - 1) * w.h * 0.6, (nz - 1) * w.h * 0.5]])
+    w.rec_xyz = w.rec_xyz[(w.rec_xyz[:, 0] <= (nx - 1) * w.h) & (w.rec_xyz[:, 1] <= (ny - 1) * w.h)]
+    return w
+
+
+@pytest.mark.parametrize("order", [4, 8, 12])
+def test_one_step_parity(fdw, O, order):
+    w = small_tti(order=order, seed=50 + order)
+    s = tti_solver(fdw, w)
+    comp = s.comp_shape
+    fields = [synth.random_wavefield(comp, 90 + i + order, scale=1e-3) for i in range(4)]
+    for (f, lvl), a in zip([(0, 0), (0, 1), (1, 0), (1, 1)], fields):
+        s.set_wavefield(a, f, lvl)
+    k = 3
+    s.set_current_step(k)
+    s.step(1)
+    got_p, got_r = s.wavefield(0, 0), s.wavefield(1, 0)
+    s.check()
+    pp, rp = O.tti_step(tti_setup(O, w), fields[0], fields[1], fields[2], fields[3], w.src_xyz,
+                        float(w.wavelet[k, 0]))
+    assert rel(got_p, pp) <= STEP_TOL, rel(got_p, pp)
+    assert rel(got_r, rp) <= STEP_TOL, rel(got_r, rp)
+    tr = s.traces()
+    np.testing.assert_allclose(tr[k + 1], O.interpolate(pp, w.rec_xyz, w.h, w.nb), rtol=0,
+                               atol=1e-5 * np.abs(pp).max())
+    s.close()
+
+
+def test_tti_run(fdw, O):
+    w = small_tti(order=8, nt=40, seed=77)
+    s = tti_solver(fdw, w)
+    s.step(w.nt)
+    ref = O.tti_forward(tti_setup(O, w), w.src_xyz, w.wavelet, w.nt, w.rec_xyz)
+    assert rel(s.traces(), ref["traces"]) <= RUN_TOL
+    assert rel(s.wavefield(0, 0), ref["p"]) <= RUN_TOL
+    assert rel(s.wavefield(1, 0), ref["r"]) <= RUN_TOL
+    assert rel(s.wavefield(1, 1), ref["rm"]) <= RUN_TOL
+    s.close()
+
+
+def test_isotropic_tti_equals_acoustic(fdw):
+    """eps = delta = 0: p = r = the acoustic solution for any tilt."""
+    w = small_tti(order=8, nt=25, seed=78)
+    w.eps = np.zeros_like(w.eps)
+    w.delta = np.zeros_like(w.delta)
+    s = tti_solver(fdw, w)
+    s.step(w.nt)
+    a = fdw.Solver(w.n, w.h, w.nb, w.order)
+    a.set_model(w.vp).set_dt(w.dt).set_sources(w.src_xyz, w.wavelet).step(w.nt)
+    ua = a.wavefield(0, 0)
+    assert rel(s.wavefield(0, 0), ua) <= 1e-5
+    assert rel(s.wavefield(1, 0), ua) <= 1e-5
+    s.close()
+    a.close()
