@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--tile", type=int, default=-1, help="2.5D kernel tile configuration (-1 default)")
+    p.add_argument("--zchunks", type=int, default=0, help="CTAs along z (0 default)")
+    p.add_argument("--no-tti", action="store_true")
+    p.add_argument("--tti-n", type=int, default=384, help="physical TTI grid points per axis")
     return p.parse_args()
 
 
@@ -67,7 +71,7 @@ def peaks():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("acoustic.cu", "ptx.cuh", "fdw_internal.h"):
+    for f in ("acoustic.cu", "acoustic_kernel.cuh", "ptx.cuh", "fdw_internal.h"):
         with open(os.path.join(ROOT, "paper_1608_03984_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -252,6 +256,8 @@ def run_fdwave(args, orders):
         s = fdwave.Solver(base.n, base.h, base.nb, o, stream=stream)
         s.set_model(base.vp).set_dt(base.dt).set_sources(base.src_xyz, base.wavelet)
         s.set_receivers(base.rec_xyz, nt)
+        s.set_tile_config(args.tile)
+        s.set_zchunks(args.zchunks)
         solvers.append(s)
 
     for s in solvers:
@@ -282,6 +288,8 @@ def run_fdwave(args, orders):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     kern = [s.profile_end() for s in solvers]
+    tiles = {o: s.tile_config for o, s in zip(orders, solvers)}
+    zchs = {o: s.zchunks for o, s in zip(orders, solvers)}
     for s in solvers:
         s.check()
     if world > 1:
@@ -301,7 +309,8 @@ def run_fdwave(args, orders):
         achieved = BYTES_PER_POINT * points / (avg / 1e3) / 1e9
         gpts_k = points / (avg / 1e3) / 1e9
         per_order[str(o)] = {
-            "kernel_ms": avg, "kernel_gpts": gpts_k, "achieved_gbs": achieved,
+            "kernel_ms": avg, "kernel_gpts": gpts_k, "tile": tiles[o], "zchunks": zchs[o],
+            "achieved_gbs": achieved,
             "frac_of_measured_hbm": achieved / hbm,
             "I_alg_paper": opmodel.oi("acoustic", k),
             "paper_model_gflops": gpts_k * opmodel.flops_per_point("acoustic", k),
@@ -322,6 +331,9 @@ def run_fdwave(args, orders):
         e2e = run_e2e(args, orders, base, stream)
     for s in solvers:
         s.close()
+    tti = None
+    if not args.no_tti:
+        tti = run_tti(args, stream, steps=min(args.steps, 30), warmup=3)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -339,13 +351,50 @@ def run_fdwave(args, orders):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_dict(args, orders, base),
-            "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu, "tti": tti,
             "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+TTI_FIELD_BYTES = 11  # TTI kernel: read p, r, p-, r-, c, e, d, nx, ny; write p+, r+
+
+
+def run_tti(args, stream, steps, warmup):
+    """The TTI workload: 384^3 + 40-point sponge (464^3), h = 12.5 m, smooth
+    random eps/delta/theta/phi, orders 8 and 12, FP32 / BF16 / FP16 storage
+    (FP32 arithmetic). Kernel time from CUDA events around each launch."""
+    import torch
+    from paper_1608_03984_gb300 import fdwave, synth
+    hbm, _ = peaks()
+    w = synth.random_tti(n=args.tti_n, nb=args.nb, order=8, nt=steps + warmup + 2, nrec_side=128)
+    out = {"workload": "random_tti %d^3 + %d-point sponge (%d^3), h=12.5 m, orders 8/12"
+                       % (args.tti_n, args.nb, w.n_comp[0]),
+           "algorithmic_bytes_per_point": {"f32": 4 * TTI_FIELD_BYTES, "bf16": 2 * TTI_FIELD_BYTES,
+                                           "f16": 2 * TTI_FIELD_BYTES},
+           "paper_model_bytes_per_point": 60}
+    for order in (8, 12):
+        for st in ("f32", "bf16", "f16"):
+            s = fdwave.Solver(w.n, w.h, w.nb, order, equation="tti", storage=st, stream=stream)
+            s.set_model(w.vp, w.eps, w.delta, w.theta, w.phi).set_dt(w.dt)
+            s.set_sources(w.src_xyz, w.wavelet).set_receivers(w.rec_xyz, w.nt)
+            s.step(warmup)
+            torch.cuda.synchronize()
+            s.profile_begin(steps)
+            s.step(steps)
+            ms, n = s.profile_end()
+            s.check()
+            s.close()
+            avg = ms / max(n, 1)
+            gpts = w.points / (avg / 1e3) / 1e9
+            bpp = (4 if st == "f32" else 2) * TTI_FIELD_BYTES
+            out.setdefault(str(order), {})[st] = {
+                "kernel_ms": avg, "gpts": gpts, "achieved_gbs": gpts * bpp,
+                "frac_of_measured_hbm": gpts * bpp / hbm}
+    return out
 
 
 def run_e2e(args, orders, base, stream):

@@ -181,6 +181,16 @@ int fdw_set_kernel_variant(fdw_solver *s, int variant);
  * returns the value in use (-1 for NULL).
  */
 int fdw_set_zchunks(fdw_solver *s, int zchunks);
+
+/*
+ * Tile configuration of the 2.5D acoustic kernel (points per thread in x/y,
+ * warps per CTA, z unrolling; see acoustic_kernel.cuh): 0..4, or -1 for the
+ * default of the solver's order and storage. Resets zchunks to its default.
+ * fdw_get_tile_config returns the configuration in use (-1 for NULL).
+ * Errors: INVALID_ARG.
+ */
+int fdw_set_tile_config(fdw_solver *s, int tile);
+int fdw_get_tile_config(const fdw_solver *s);
 int fdw_get_zchunks(const fdw_solver *s);
 
 /*

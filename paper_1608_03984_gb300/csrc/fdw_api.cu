@@ -76,8 +76,10 @@ struct fdw_solver {
 
   Weights w;
   int zchunks = 0;
+  int tile = 0;  // configuration of the 2.5D acoustic kernel
   int naive = 0;
   CUtensorMap map_halo[2][2], map_int[2][2], map_c;  // [field][buffer]
+  CUtensorMap map_e, map_dl, map_ax, map_ay;          // TTI medium
   bool maps_ok = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_ok = false;
@@ -180,8 +182,11 @@ int make_map(CUtensorMap *m, const fdw_solver *s, void *base, int bx, int by) {
 
 int build_maps(fdw_solver *s) {
   if (s->maps_ok) return FDW_OK;
-  int bhx, bhy, bix, biy;
-  acoustic_tile(s->storage, s->r, &bhx, &bhy, &bix, &biy);
+  TileGeom tg;
+  const int bad = s->eq == FDW_TTI ? tti_geom(s->storage, s->r, &tg)
+                                   : acoustic_geom(s->storage, s->r, s->tile, &tg);
+  if (bad) return fail(FDW_ERR_INVALID_ARG, "bad tile");
+  const int bhx = tg.box_halo_x, bhy = tg.box_halo_y, bix = tg.box_int_x, biy = tg.box_int_y;
   const int nf = s->eq == FDW_TTI ? 2 : 1;
   for (int f = 0; f < nf; ++f)
     for (int b = 0; b < 2; ++b) {
@@ -192,6 +197,12 @@ int build_maps(fdw_solver *s) {
     }
   int rc = make_map(&s->map_c, s, s->c, bix, biy);
   if (rc) return rc;
+  if (s->eq == FDW_TTI) {
+    if ((rc = make_map(&s->map_e, s, s->e, bix, biy))) return rc;
+    if ((rc = make_map(&s->map_dl, s, s->dl, bix, biy))) return rc;
+    if ((rc = make_map(&s->map_ax, s, s->ax, bix, biy))) return rc;
+    if ((rc = make_map(&s->map_ay, s, s->ay, bix, biy))) return rc;
+  }
   s->maps_ok = true;
   return FDW_OK;
 }
@@ -205,9 +216,16 @@ void drop_graphs(fdw_solver *s) {
   s->graph_ok = false;
 }
 
+// A CTA marches at most kMaxZChunk planes (its damping slice lives in
+// shared memory).
+int min_zchunks(const fdw_solver *s) { return (s->d.NZ + kMaxZChunk - 1) / kMaxZChunk; }
+
 int default_zchunks(const fdw_solver *s) {
-  int bhx, bhy, bix, biy;
-  acoustic_tile(s->storage, s->r, &bhx, &bhy, &bix, &biy);
+  TileGeom tg;
+  const int bad = s->eq == FDW_TTI ? tti_geom(s->storage, s->r, &tg)
+                                   : acoustic_geom(s->storage, s->r, s->tile, &tg);
+  if (bad) return 1;
+  const int bix = tg.box_int_x, biy = tg.box_int_y;
   const long tiles = (long)((s->d.NX + bix - 1) / bix) * ((s->d.NY + biy - 1) / biy);
   long want = (152L * 16 + tiles - 1) / tiles;  // about 16 CTAs per SM in total
   const int zmin = 4 * s->r > 16 ? 4 * s->r : 16;
@@ -215,14 +233,14 @@ int default_zchunks(const fdw_solver *s) {
   if (maxch < 1) maxch = 1;
   if (want > maxch) want = maxch;
   if (want < 1) want = 1;
-  return (int)want;
+  return min_zchunks(s) > want ? min_zchunks(s) : (int)want;
 }
 
 // Enqueue the stencil update of one time step from buffer `cur` on stream st.
 int enqueue_stencil(fdw_solver *s, int cur, cudaStream_t st) {
   const int nxt = 1 - cur;
   if (s->eq == FDW_ACOUSTIC) {
-    AcousticLaunch L;
+    AcousticLaunch L{};
     L.storage = s->storage;
     L.r = s->r;
     L.d = s->d;
@@ -238,9 +256,10 @@ int enqueue_stencil(fdw_solver *s, int cur, cudaStream_t st) {
     L.zchunks = s->zchunks;
     L.err = s->d_err;
     L.naive = s->naive;
+    L.tile = s->tile;
     CK(launch_acoustic(L, st));
   } else {
-    TTILaunch L;
+    TTILaunch L{};
     L.storage = s->storage;
     L.r = s->r;
     L.d = s->d;
@@ -255,6 +274,15 @@ int enqueue_stencil(fdw_solver *s, int cur, cudaStream_t st) {
     L.dl = s->dl;
     L.ax = s->ax;
     L.ay = s->ay;
+    L.m_ph = &s->map_halo[0][cur];
+    L.m_rh = &s->map_halo[1][cur];
+    L.m_pm = &s->map_int[0][nxt];
+    L.m_rm = &s->map_int[1][nxt];
+    L.m_c = &s->map_c;
+    L.m_e = &s->map_e;
+    L.m_d = &s->map_dl;
+    L.m_ax = &s->map_ax;
+    L.m_ay = &s->map_ay;
     L.zchunks = s->zchunks;
     L.err = s->d_err;
     L.naive = s->naive;
@@ -266,7 +294,7 @@ int enqueue_stencil(fdw_solver *s, int cur, cudaStream_t st) {
 // Enqueue the sparse work (injection, receivers) after the update from `cur`.
 int enqueue_sparse(fdw_solver *s, int cur, cudaStream_t st) {
   const int nxt = 1 - cur;
-  SparseLaunch S;
+  SparseLaunch S{};
   memset(&S, 0, sizeof S);
   S.storage = s->storage;
   S.d = s->d;
@@ -436,6 +464,7 @@ extern "C" int fdw_create(fdw_solver **out, int nx, int ny, int nz, double h, in
     fdw_destroy(s);
     return rc;
   }
+  s->tile = acoustic_default_tile(storage, s->r);
   s->zchunks = default_zchunks(s);
   const char *nv = getenv("FDW_KERNEL");
   s->naive = (nv && strcmp(nv, "naive") == 0) ? 1 : 0;
@@ -632,7 +661,7 @@ static int ensure_graphs(fdw_solver *s) {
   int rc = build_maps(s);
   if (rc) return rc;
   // kernel attributes (large dynamic shared memory) are set outside capture
-  CK(s->eq == FDW_ACOUSTIC ? acoustic_prepare(s->storage, s->r) : tti_prepare(s->storage, s->r));
+  CK(s->eq == FDW_ACOUSTIC ? acoustic_prepare(s->storage, s->r, s->tile) : tti_prepare(s->storage, s->r));
   for (int b = 0; b < 2; ++b) {
     cudaGraph_t gr = nullptr;
     CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
@@ -812,8 +841,26 @@ extern "C" int fdw_set_kernel_variant(fdw_solver *s, int variant) {
   return FDW_OK;
 }
 
+extern "C" int fdw_set_tile_config(fdw_solver *s, int tile) {
+  if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
+  TileGeom tg;
+  if (tile < -1 || tile >= kAcTiles ||
+      (tile >= 0 && acoustic_geom(s->storage, s->r, tile, &tg)))
+    return fail(FDW_ERR_INVALID_ARG, "tile configuration must be -1 (default) or 0..%d", kAcTiles - 1);
+  s->tile = tile < 0 ? acoustic_default_tile(s->storage, s->r) : tile;
+  s->maps_ok = false;
+  s->zchunks = default_zchunks(s);
+  drop_graphs(s);
+  return FDW_OK;
+}
+
+extern "C" int fdw_get_tile_config(const fdw_solver *s) { return s ? s->tile : -1; }
+
 extern "C" int fdw_set_zchunks(fdw_solver *s, int zchunks) {
   if (!s || zchunks < 0) return fail(FDW_ERR_INVALID_ARG, "zchunks must be >= 0");
+  if (zchunks > 0 && zchunks < min_zchunks(s))
+    return fail(FDW_ERR_INVALID_ARG, "zchunks must be >= %d (at most %d planes per CTA)",
+                min_zchunks(s), kMaxZChunk);
   s->zchunks = zchunks == 0 ? default_zchunks(s) : zchunks;
   drop_graphs(s);
   return FDW_OK;

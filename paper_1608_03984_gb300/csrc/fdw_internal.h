@@ -12,6 +12,7 @@ namespace fdw {
 
 constexpr int kMaxR = 8;          // space order 16
 constexpr int kTileX = 32;        // x extent of a stencil tile (one warp)
+constexpr int kMaxZChunk = 1024;  // most z planes one CTA of a 2.5D kernel marches
 
 // Device error flags (bit mask written with atomicOr).
 constexpr int kErrWaitTimeout = 1;  // an mbarrier wait gave up
@@ -75,14 +76,27 @@ struct AcousticLaunch {
   int *err;               // device error flags
   int naive;              // 1 = one-thread-per-point kernel (debug cross-check)
   int prepare_only;       // 1 = only set kernel attributes (outside graph capture)
+  int tile;               // tile configuration index of the 2.5D kernel
 };
 cudaError_t launch_acoustic(const AcousticLaunch &L, cudaStream_t st);
-cudaError_t acoustic_prepare(int storage, int r);
+cudaError_t acoustic_prepare(int storage, int r, int tile);
 
-// Tile geometry of the 2.5D acoustic kernel for radius r and storage type,
-// used by the host to build the tensor maps.
-void acoustic_tile(int storage, int r, int *box_halo_x, int *box_halo_y, int *box_int_x,
-                   int *box_int_y);
+// Tile geometry of one configuration of the 2.5D acoustic kernel: the TMA
+// boxes (halo tile and interior tiles) the host encodes in tensor maps.
+struct TileGeom {
+  int box_halo_x, box_halo_y, box_int_x, box_int_y, smem;
+};
+constexpr int kAcTiles = 5;  // number of configurations (see acoustic_kernel.cuh)
+// 0 on success, -1 for an unknown (storage, r, tile).
+int acoustic_geom(int storage, int r, int tile, TileGeom *g);
+// Default configuration for (storage, r).
+int acoustic_default_tile(int storage, int r);
+cudaError_t launch_acoustic_f32(const AcousticLaunch &L, cudaStream_t st);
+cudaError_t launch_acoustic_bf16(const AcousticLaunch &L, cudaStream_t st);
+cudaError_t launch_acoustic_f16(const AcousticLaunch &L, cudaStream_t st);
+int acoustic_geom_f32(int r, int tile, TileGeom *g);
+int acoustic_geom_bf16(int r, int tile, TileGeom *g);
+int acoustic_geom_f16(int r, int tile, TileGeom *g);
 
 // TTI step (Eq. TTI / Eq. DiffOp + sponge).
 struct TTILaunch {
@@ -102,9 +116,19 @@ struct TTILaunch {
   int *err;
   int naive;
   int prepare_only;
+  // tensor maps: halo tiles of p, r at level n; interior tiles of p, r at
+  // level n-1 and of the medium fields
+  const CUtensorMap *m_ph, *m_rh, *m_pm, *m_rm, *m_c, *m_e, *m_d, *m_ax, *m_ay;
 };
 cudaError_t launch_tti(const TTILaunch &L, cudaStream_t st);
 cudaError_t tti_prepare(int storage, int r);
+int tti_geom(int storage, int r, TileGeom *g);
+cudaError_t launch_tti_tma_f32(const TTILaunch &L, cudaStream_t st);
+cudaError_t launch_tti_tma_bf16(const TTILaunch &L, cudaStream_t st);
+cudaError_t launch_tti_tma_f16(const TTILaunch &L, cudaStream_t st);
+int tti_geom_f32(int r, TileGeom *g);
+int tti_geom_bf16(int r, TileGeom *g);
+int tti_geom_f16(int r, TileGeom *g);
 
 // Sparse work of one step (after the stencil update):
 //   inject: u+ += c w_corner amp / (h P) at each source corner (both p and r

@@ -18,7 +18,8 @@
 namespace fdw {
 
 // One thread per point, plain global loads: the cross derivatives are the
-// full (2r)^2-tap tensor products. A GPU cross-check of the fast kernel.
+// full (2r)^2-tap tensor products. A GPU cross-check of the 2.5D kernel of
+// tti_kernel.cuh (instantiated per storage in tti_{f32,bf16,f16}.cu).
 template <typename T, int R>
 __global__ void __launch_bounds__(256)
     tti_naive_kernel(const T *__restrict__ pc, T *__restrict__ pp, const T *__restrict__ rc,
@@ -77,7 +78,6 @@ __global__ void __launch_bounds__(256)
 
 template <typename T, int R>
 static cudaError_t launch_r(const TTILaunch &L, cudaStream_t st) {
-  if (L.prepare_only) return cudaSuccess;
   dim3 blk(32, 8), grd((L.d.NX + 31) / 32, (L.d.NY + 7) / 8, L.d.NZ);
   tti_naive_kernel<T, R><<<grd, blk, 0, st>>>(
       (const T *)L.p_cur, (T *)L.p_prev, (const T *)L.r_cur, (T *)L.r_prev, (const T *)L.c,
@@ -86,7 +86,7 @@ static cudaError_t launch_r(const TTILaunch &L, cudaStream_t st) {
 }
 
 template <typename T>
-static cudaError_t launch_t(const TTILaunch &L, cudaStream_t st) {
+static cudaError_t launch_naive_t(const TTILaunch &L, cudaStream_t st) {
   switch (L.r) {
     case 1: return launch_r<T, 1>(L, st);
     case 2: return launch_r<T, 2>(L, st);
@@ -101,16 +101,33 @@ static cudaError_t launch_t(const TTILaunch &L, cudaStream_t st) {
 }
 
 cudaError_t launch_tti(const TTILaunch &L, cudaStream_t st) {
+  if (L.naive && !L.prepare_only) {
+    switch (L.storage) {
+      case FDW_F32: return launch_naive_t<float>(L, st);
+      case FDW_BF16: return launch_naive_t<__nv_bfloat16>(L, st);
+      case FDW_F16: return launch_naive_t<__half>(L, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (L.storage) {
-    case FDW_F32: return launch_t<float>(L, st);
-    case FDW_BF16: return launch_t<__nv_bfloat16>(L, st);
-    case FDW_F16: return launch_t<__half>(L, st);
+    case FDW_F32: return launch_tti_tma_f32(L, st);
+    case FDW_BF16: return launch_tti_tma_bf16(L, st);
+    case FDW_F16: return launch_tti_tma_f16(L, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
+int tti_geom(int storage, int r, TileGeom *g) {
+  switch (storage) {
+    case FDW_F32: return tti_geom_f32(r, g);
+    case FDW_BF16: return tti_geom_bf16(r, g);
+    case FDW_F16: return tti_geom_f16(r, g);
+    default: return -1;
+  }
+}
+
 cudaError_t tti_prepare(int storage, int r) {
-  TTILaunch L;
+  TTILaunch L{};
   memset(&L, 0, sizeof L);
   L.storage = storage;
   L.r = r;

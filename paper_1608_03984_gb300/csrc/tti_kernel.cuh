@@ -1,0 +1,345 @@
+// tti_kernel.cuh -- the 2.5D z-marching TTI step kernel (template).
+//
+// Eq. TTI with the rotated operators of Eq. DiffOp and the fused sponge:
+//   P p+ = 2p - Q p- + c [ e H p + d G r ]
+//   P r+ = 2r - Q r- + c [ d H p + G r ]
+//   G f = sum_ij n_i n_j D_ij f,   H f = (Gxx + Gyy) f = lap f - G f,
+// n = (sin t cos f, sin t sin f, cos t), e = 1 + 2 eps, d = sqrt(1 + 2 delta).
+// D_ii is the k-point second-derivative stencil, D_ij (i != j) the tensor
+// product of the k-point first-derivative stencils D_i D_j, evaluated here
+// in factored form (first derivative of a first derivative): the same
+// discrete operator with O(k) instead of O(k^2) operations per point.
+//
+// Geometry. A CTA owns a 32 x TY column (one point per thread) and marches a
+// chunk of z planes. Everything that needs x/y neighbours is computed when a
+// plane enters the march as the HEAD plane z+r, from one TMA halo tile per
+// field:
+//   f_xx, f_yy, D_x f, D_y f, and D_x(D_y f) (through a shared scratch of
+//   D_y f that includes the x halo), folded with that plane's axis into
+//   A f = nx^2 f_xx + ny^2 f_yy + 2 nx ny f_xy   (in-plane part of G f);
+// f, D_x f, D_y f enter register queues of 2r + U planes and the in-plane
+// sums (f_xx + f_yy - A f for p, A f for r) a delay queue of r + U planes.
+// When the plane is the OUTPUT plane z, the z parts follow from the queues:
+//   f_zz, D_z(D_x f), D_z(D_y f), and
+//   H p = [p_xx + p_yy - A p] + (1 - nz^2) p_zz - 2 nx nz p_xz - 2 ny nz p_yz
+//   G r = [A r] + nz^2 r_zz + 2 nx nz r_xz + 2 ny nz r_yz.
+// The axis is stored as (nx, ny) with nz = sqrt(1 - nx^2 - ny^2) >= 0
+// (n n^T does not depend on the sign of n).
+//
+// Each TMA stage holds: the p and r halo tiles and the (nx, ny) tiles of the
+// head plane; the p-, r-, c, e, d, nx, ny tiles of the output plane. Every
+// mbarrier wait is bounded (error flag, drain, exit).
+#pragma once
+
+#include "fdw_internal.h"
+#include "fdwave.h"
+#include "ptx.cuh"
+
+namespace fdw {
+
+template <typename T, int R, int BY, int NS, int U>
+struct TtiTile {
+  static constexpr int TX = 32;
+  static constexpr int TY = BY;
+  static constexpr int EL = (int)sizeof(T);
+  static constexpr int XALIGN = 16 / EL;
+  static constexpr int HX = ((R + XALIGN - 1) / XALIGN) * XALIGN;
+  static constexpr int BXH = TX + 2 * HX;
+  static constexpr int BYH = TY + 2 * R;
+  static constexpr int a128(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int HALO_B = a128(BXH * BYH * EL);
+  static constexpr int INT_B = a128(TX * TY * EL);
+  // slot: halo p | halo r | head nx, ny | out pm, rm, c, e, d, nx, ny
+  static constexpr int N_INT = 9;
+  static constexpr int STAGE_B = 2 * HALO_B + N_INT * INT_B;
+  static constexpr int SY = TX + 2 * R;  // row length of the D_y scratch
+  static constexpr int SCR_B = a128(2 * TY * SY * 4);
+  static constexpr int BAR_B = 128;
+  static constexpr int SMEM_B = NS * STAGE_B + SCR_B + BAR_B + kMaxZChunk * 4 + 128;
+  static constexpr int THREADS = 32 * BY;
+  static constexpr int QL = 2 * R + U;
+  static constexpr int DL = R + U;
+  static_assert(NS >= 2, "ring needs two stages");
+  static_assert(BXH <= 256 && BYH <= 256, "TMA box dimension limit");
+  static_assert((BXH * EL) % 16 == 0 && (TX * EL) % 16 == 0 && (HX * EL) % 16 == 0, "TMA alignment");
+  static_assert(SMEM_B <= 227 * 1024, "shared memory per CTA");
+  static_assert(2 * 2 * R * TY <= THREADS * 4, "halo columns of D_y per thread");
+};
+
+template <typename T, int R, int BY, int NS, int U>
+__global__ void __launch_bounds__(32 * BY)
+    tti_tma_kernel(const __grid_constant__ CUtensorMap m_ph, const __grid_constant__ CUtensorMap m_rh,
+                   const __grid_constant__ CUtensorMap m_pm, const __grid_constant__ CUtensorMap m_rm,
+                   const __grid_constant__ CUtensorMap m_c, const __grid_constant__ CUtensorMap m_e,
+                   const __grid_constant__ CUtensorMap m_d, const __grid_constant__ CUtensorMap m_ax,
+                   const __grid_constant__ CUtensorMap m_ay, T *__restrict__ p_out,
+                   T *__restrict__ r_out, Dims d, Weights w, Sponge sp, int zc, int *err) {
+  using C = TtiTile<T, R, BY, NS, U>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  float *scr = (float *)(smem + NS * C::STAGE_B);  // [2][TY][SY] D_y of p and r
+  uint64_t *bars = (uint64_t *)(smem + NS * C::STAGE_B + C::SCR_B);
+  float *gzs = (float *)(smem + NS * C::STAGE_B + C::SCR_B + C::BAR_B);
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.NZ);
+  if (z0 >= z1 || zc > kMaxZChunk) return;  // uniform over the CTA
+  const int nit = (z1 - z0) + 2 * R;
+  const float gxr = (x0 + tx < d.NX) ? sp.gx[x0 + tx] : 0.f;
+  const float gyr = (y0 + ty < d.NY) ? sp.gy[y0 + ty] : 0.f;
+
+  const CUtensorMap *maps_int[C::N_INT] = {&m_ax, &m_ay, &m_pm, &m_rm, &m_c, &m_e, &m_d, &m_ax, &m_ay};
+  if (tid == 0) {
+    prefetch_tensormap(&m_ph);
+    prefetch_tensormap(&m_rh);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) prefetch_tensormap(maps_int[2 + i]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    fence_barrier_init();
+  }
+  for (int i = tid; i < z1 - z0; i += C::THREADS) gzs[i] = sp.gz[z0 + i];
+  __syncthreads();
+
+  int issued_hi = -1;
+  auto issue = [&](int j) {
+    const int s = j % NS;
+    const int zh = z0 - R + j;
+    const bool head = (zh >= 0 && zh < d.NZ);
+    const bool outp = (j >= 2 * R);
+    const uint32_t bytes = (head ? (2 * C::BXH * C::BYH + 2 * C::TX * C::TY) * C::EL : 0) +
+                           (outp ? 7 * C::TX * C::TY * C::EL : 0);
+    const uint32_t bar = smem_u32(&bars[s]);
+    unsigned char *st = smem + s * C::STAGE_B;
+    mbar_arrive_expect_tx(bar, bytes);
+    if (head) {
+      tma_load_3d(smem_u32(st), &m_ph, x0 - C::HX, y0 - R, zh, bar);
+      tma_load_3d(smem_u32(st + C::HALO_B), &m_rh, x0 - C::HX, y0 - R, zh, bar);
+      tma_load_3d(smem_u32(st + 2 * C::HALO_B + 0 * C::INT_B), &m_ax, x0, y0, zh, bar);
+      tma_load_3d(smem_u32(st + 2 * C::HALO_B + 1 * C::INT_B), &m_ay, x0, y0, zh, bar);
+    }
+    if (outp) {
+      const int zo = zh - R;
+#pragma unroll
+      for (int i = 2; i < C::N_INT; ++i)
+        tma_load_3d(smem_u32(st + 2 * C::HALO_B + i * C::INT_B), maps_int[i], x0, y0, zo, bar);
+    }
+    issued_hi = j;
+  };
+  if (tid == 0) {
+    const int n0 = nit < NS ? nit : NS;
+    for (int j = 0; j < n0; ++j) issue(j);
+  }
+
+  // queues: [0] p, [1] D_x p, [2] D_y p, [3] r, [4] D_x r, [5] D_y r
+  float q[6][C::QL];
+  float dq[2][C::DL];  // delayed in-plane sums: p_xx + p_yy - A p, A r
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int i = 0; i < C::QL; ++i) q[a][i] = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int i = 0; i < C::DL; ++i) dq[a][i] = 0.f;
+
+  const size_t plane = d.plane();
+  const int li = ty * C::TX + tx;  // index inside an interior tile
+
+#pragma unroll 1
+  for (int j0 = 0; j0 < nit; j0 += U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u;
+      if (j >= nit) break;  // uniform
+      const int s = j % NS;
+      const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((j / NS) & 1));
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(err, kErrWaitTimeout);
+          for (int jj = j; jj <= issued_hi; ++jj)
+            (void)mbar_wait_bounded(smem_u32(&bars[jj % NS]), (uint32_t)((jj / NS) & 1));
+        }
+        return;
+      }
+      if (tid == 0 && j >= 1 && j - 1 + NS < nit) issue(j - 1 + NS);
+
+      const unsigned char *st = smem + s * C::STAGE_B;
+      const int zh = z0 - R + j;
+      const bool head = (zh >= 0 && zh < d.NZ);
+      if (head) {
+        float fxx[2], fyy[2];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          const T *H = (const T *)(st + f * C::HALO_B);
+          const T *row = H + (ty + R) * C::BXH + C::HX + tx;
+          const float fc = St<T>::ld(row[0]);
+          float xx = w.w2[0] * fc, yy = w.w2[0] * fc, dx = 0.f, dy = 0.f;
+#pragma unroll
+          for (int m = 1; m <= R; ++m) {
+            const float xp = St<T>::ld(row[m]), xm = St<T>::ld(row[-m]);
+            const float yp = St<T>::ld(row[m * C::BXH]), ym = St<T>::ld(row[-m * C::BXH]);
+            xx = fmaf(w.w2[m], xp + xm, xx);
+            dx = fmaf(w.c1[m], xp - xm, dx);
+            yy = fmaf(w.w2[m], yp + ym, yy);
+            dy = fmaf(w.c1[m], yp - ym, dy);
+          }
+          fxx[f] = xx;
+          fyy[f] = yy;
+          q[3 * f + 0][2 * R + u] = fc;
+          q[3 * f + 1][2 * R + u] = dx;
+          q[3 * f + 2][2 * R + u] = dy;
+          scr[(f * C::TY + ty) * C::SY + R + tx] = dy;
+        }
+        // D_y of both fields in the x halo columns [-R, 0) and [32, 32 + R)
+        for (int t = tid; t < 2 * 2 * R * C::TY; t += C::THREADS) {
+          const int f = t / (2 * R * C::TY);
+          const int rem = t - f * (2 * R * C::TY);
+          const int yy_ = rem / (2 * R);
+          const int k = rem - yy_ * (2 * R);
+          const int xo = k < R ? k - R : C::TX + (k - R);  // tile x of the halo column
+          const T *H = (const T *)(st + f * C::HALO_B);
+          const T *col = H + (yy_ + R) * C::BXH + C::HX + xo;
+          float dy = 0.f;
+#pragma unroll
+          for (int m = 1; m <= R; ++m)
+            dy = fmaf(w.c1[m], St<T>::ld(col[m * C::BXH]) - St<T>::ld(col[-m * C::BXH]), dy);
+          scr[(f * C::TY + yy_) * C::SY + R + xo] = dy;
+        }
+        __syncthreads();
+        const T *HA = (const T *)(st + 2 * C::HALO_B);
+        const float hx = St<T>::ld(HA[li]), hy = St<T>::ld(HA[C::INT_B / C::EL + li]);
+        float A[2];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          const float *sr = scr + (f * C::TY + ty) * C::SY + R + tx;
+          float xy = 0.f;
+#pragma unroll
+          for (int m = 1; m <= R; ++m) xy = fmaf(w.c1[m], sr[m] - sr[-m], xy);
+          A[f] = hx * hx * fxx[f] + hy * hy * fyy[f] + 2.f * hx * hy * xy;
+        }
+        dq[0][R + u] = fxx[0] + fyy[0] - A[0];
+        dq[1][R + u] = A[1];
+      } else {
+#pragma unroll
+        for (int a = 0; a < 6; ++a) q[a][2 * R + u] = 0.f;
+        dq[0][R + u] = 0.f;
+        dq[1][R + u] = 0.f;
+      }
+      if (j < 2 * R) continue;
+
+      // output plane zo = zh - R
+      const int zo = zh - R;
+      const T *O = (const T *)(st + 2 * C::HALO_B);
+      auto tileval = [&](int i) { return St<T>::ld(O[i * (C::INT_B / C::EL) + li]); };
+      const float pm = tileval(2), rm = tileval(3), cc = tileval(4), ee = tileval(5), dd = tileval(6);
+      const float nx = tileval(7), ny = tileval(8);
+      const float nz = sqrtf(fmaxf(0.f, 1.f - nx * nx - ny * ny));
+      float zz[2], xz[2], yz[2];
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        float a = w.w2[0] * q[3 * f][u + R], b = 0.f, c = 0.f;
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+          a = fmaf(w.w2[m], q[3 * f][u + R + m] + q[3 * f][u + R - m], a);
+          b = fmaf(w.c1[m], q[3 * f + 1][u + R + m] - q[3 * f + 1][u + R - m], b);
+          c = fmaf(w.c1[m], q[3 * f + 2][u + R + m] - q[3 * f + 2][u + R - m], c);
+        }
+        zz[f] = a;
+        xz[f] = b;
+        yz[f] = c;
+      }
+      const float Hp = dq[0][u] + (1.f - nz * nz) * zz[0] - 2.f * nz * (nx * xz[0] + ny * yz[0]);
+      const float Gr = dq[1][u] + nz * nz * zz[1] + 2.f * nz * (nx * xz[1] + ny * yz[1]);
+      const float gh = gxr + gyr + gzs[zo - z0];
+      const float inv = __fdividef(1.f, 1.f + gh), qq = 1.f - gh;
+      const float pn = (2.f * q[0][u + R] - qq * pm + cc * (ee * Hp + dd * Gr)) * inv;
+      const float rn = (2.f * q[3][u + R] - qq * rm + cc * (dd * Hp + Gr)) * inv;
+      const int x = x0 + tx, y = y0 + ty;
+      if (x < d.NX && y < d.NY) {
+        const size_t o = (size_t)zo * plane + (size_t)y * d.Xp + x;
+        p_out[o] = St<T>::st(pn);
+        r_out[o] = St<T>::st(rn);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i) q[a][i] = q[a][i + U];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int i = 0; i < R; ++i) dq[a][i] = dq[a][i + U];
+  }
+}
+
+}  // namespace fdw
+
+namespace fdw {
+
+constexpr int kTtiNS = 4;
+constexpr int kTtiU = 2;
+template <int R> struct TtiCfg {
+  static constexpr int BY = 8;
+};
+
+template <typename T, int R>
+cudaError_t launch_tti_tma(const TTILaunch &L, cudaStream_t st) {
+  constexpr int BY = TtiCfg<R>::BY;
+  using C = TtiTile<T, R, BY, kTtiNS, kTtiU>;
+  auto kern = tti_tma_kernel<T, R, BY, kTtiNS, kTtiU>;
+  if (L.prepare_only)
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_B);
+  const int zch = L.zchunks < 1 ? 1 : L.zchunks;
+  const int zc = (L.d.NZ + zch - 1) / zch;
+  if (zc > kMaxZChunk) return cudaErrorInvalidValue;
+  dim3 grd((L.d.NX + C::TX - 1) / C::TX, (L.d.NY + C::TY - 1) / C::TY, (L.d.NZ + zc - 1) / zc);
+  dim3 blk(32, BY);
+  kern<<<grd, blk, C::SMEM_B, st>>>(*L.m_ph, *L.m_rh, *L.m_pm, *L.m_rm, *L.m_c, *L.m_e, *L.m_d,
+                                     *L.m_ax, *L.m_ay, (T *)L.p_prev, (T *)L.r_prev, L.d, L.w,
+                                     L.sp, zc, L.err);
+  return cudaGetLastError();
+}
+
+template <typename T, int R>
+void tti_geom_r(TileGeom *g) {
+  using C = TtiTile<T, R, TtiCfg<R>::BY, kTtiNS, kTtiU>;
+  g->box_halo_x = C::BXH;
+  g->box_halo_y = C::BYH;
+  g->box_int_x = C::TX;
+  g->box_int_y = C::TY;
+  g->smem = C::SMEM_B;
+}
+
+#define FDW_TTI_DEFINE_STORAGE(SUFFIX, TYPE)                                  \
+  cudaError_t launch_tti_tma_##SUFFIX(const TTILaunch &L, cudaStream_t st) {  \
+    switch (L.r) {                                                            \
+      case 1: return launch_tti_tma<TYPE, 1>(L, st);                          \
+      case 2: return launch_tti_tma<TYPE, 2>(L, st);                          \
+      case 3: return launch_tti_tma<TYPE, 3>(L, st);                          \
+      case 4: return launch_tti_tma<TYPE, 4>(L, st);                          \
+      case 5: return launch_tti_tma<TYPE, 5>(L, st);                          \
+      case 6: return launch_tti_tma<TYPE, 6>(L, st);                          \
+      case 7: return launch_tti_tma<TYPE, 7>(L, st);                          \
+      case 8: return launch_tti_tma<TYPE, 8>(L, st);                          \
+      default: return cudaErrorInvalidValue;                                  \
+    }                                                                         \
+  }                                                                           \
+  int tti_geom_##SUFFIX(int r, TileGeom *g) {                                 \
+    switch (r) {                                                              \
+      case 1: tti_geom_r<TYPE, 1>(g); return 0;                               \
+      case 2: tti_geom_r<TYPE, 2>(g); return 0;                               \
+      case 3: tti_geom_r<TYPE, 3>(g); return 0;                               \
+      case 4: tti_geom_r<TYPE, 4>(g); return 0;                               \
+      case 5: tti_geom_r<TYPE, 5>(g); return 0;                               \
+      case 6: tti_geom_r<TYPE, 6>(g); return 0;                               \
+      case 7: tti_geom_r<TYPE, 7>(g); return 0;                               \
+      case 8: tti_geom_r<TYPE, 8>(g); return 0;                               \
+      default: return -1;                                                     \
+    }                                                                         \
+  }
+
+}  // namespace fdw

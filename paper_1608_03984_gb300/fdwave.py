@@ -52,6 +52,8 @@ _SIGS = {
     "fdw_set_kernel_variant": ([_P, _I], _I),
     "fdw_set_zchunks": ([_P, _I], _I),
     "fdw_get_zchunks": ([_P], _I),
+    "fdw_set_tile_config": ([_P, _I], _I),
+    "fdw_get_tile_config": ([_P], _I),
     "fdw_profile_begin": ([_P, _I], _I),
     "fdw_profile_end": ([_P, ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
 }
@@ -257,6 +259,14 @@ class Solver:
 
     def set_zchunks(self, zchunks):
         _chk(lib().fdw_set_zchunks(self._h, int(zchunks)))
+
+    def set_tile_config(self, tile):
+        """Tile configuration 0..4 of the 2.5D kernel, -1 = default."""
+        _chk(lib().fdw_set_tile_config(self._h, int(tile)))
+
+    @property
+    def tile_config(self):
+        return lib().fdw_get_tile_config(self._h)
 
     @property
     def zchunks(self):

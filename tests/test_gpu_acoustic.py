@@ -251,3 +251,54 @@ def test_full_size_sampled_step(fdw, O):
         worst = max(worst, abs(got - exp) / np.abs(blk).max())
     assert worst < 1e-5, worst
     s.close()
+
+
+def test_profiled_steps_match_graph_steps(fdw):
+    """Steps launched one by one under kernel timing, with several solvers
+    interleaved on one stream, are bit-identical to the CUDA-graph steps."""
+    P = random_problem(seed=10, nt=30)
+    orders = (2, 8, 16)
+    a = [make_solver(fdw, dict(P, order=o)) for o in orders]
+    b = [make_solver(fdw, dict(P, order=o)) for o in orders]
+    for s in a + b:
+        s.step(5)
+    for s in a:
+        s.profile_begin(20)
+    for _ in range(20):
+        for s in a:
+            s.step(1)
+    for s in a:
+        ms, n = s.profile_end()
+        assert n == 20 and ms > 0
+    for s in b:
+        s.step(20)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x.wavefield(0, 0), y.wavefield(0, 0))
+        np.testing.assert_array_equal(x.wavefield(0, 1), y.wavefield(0, 1))
+        np.testing.assert_array_equal(x.traces(), y.traces())
+    for s in a + b:
+        s.close()
+
+
+@pytest.mark.parametrize("order", [2, 6, 8, 16])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+def test_every_tile_configuration(fdw, O, order, tile):
+    """Each tile configuration of the 2.5D kernel (points per thread, warps
+    per CTA, z unrolling) reproduces the oracle's step on a grid with ragged
+    tails in x, y and z."""
+    P = random_problem(shape=(37, 19, 141), nb=3, order=order, seed=20 + tile, nt=8)
+    s = make_solver(fdw, P)
+    s.set_tile_config(tile)
+    assert s.tile_config == tile
+    comp = s.comp_shape
+    u = synth.random_wavefield(comp, 31, scale=1e-3)
+    um = synth.random_wavefield(comp, 32, scale=1e-3)
+    s.set_wavefield(u, 0, 0)
+    s.set_wavefield(um, 0, 1)
+    s.set_current_step(2)
+    s.step(1)
+    exp = O.acoustic_step(oracle_setup(O, P), u, um, P["src"], float(P["w"][2, 0]))
+    assert rel(s.wavefield(0, 0), exp) <= STEP_TOL
+    s.step(3)
+    s.check()
+    s.close()
