@@ -105,6 +105,15 @@ int fdw_set_model(fdw_solver *s, const float *vp, const float *eps, const float 
 double fdw_max_stable_dt(const fdw_solver *s);
 
 /*
+ * Sponge strength: gamma_max = 3 vref ln(1/R) / (2 nb h) (linear ramp over
+ * the nb points of each face). vref <= 0 (the default) uses the model's
+ * largest velocity; a fixed vref keeps the damping independent of the model
+ * (for gradients w.r.t. the model). Default R = 1e-3. Takes effect at the
+ * next fdw_set_dt (dt is marked unset). Errors: INVALID_ARG.
+ */
+int fdw_set_sponge(fdw_solver *s, double vref, double R);
+
+/*
  * Set dt (seconds): computes c = dt^2 v^2 and the sponge damping.
  * Errors: UNSTABLE_DT if dt > fdw_max_stable_dt, STATE before set_model.
  */
@@ -192,6 +201,66 @@ int fdw_set_zchunks(fdw_solver *s, int zchunks);
 int fdw_set_tile_config(fdw_solver *s, int tile);
 int fdw_get_tile_config(const fdw_solver *s);
 int fdw_get_zchunks(const fdw_solver *s);
+
+/*
+ * ---- Adjoint and FWI gradient (acoustic) ----------------------------------
+ * The paper motivates the solvers by FWI/RTM (Introduction) but states no
+ * adjoint; these calls give the exact transpose of the discrete recurrence
+ * above. For a residual res [(nt+1)][nrec] (dJ/d traces) the multipliers
+ * mu_k (k = nt .. 1, mu_{nt+1} = mu_{nt+2} = 0) obey the same step run
+ * backwards:  P mu_k = 2 mu_{k+1} - Q mu_{k+2} + c (lap mu_{k+1} + R^T res_k),
+ * R^T spreading each residual with the trilinear weights (no 1/h^3). Then
+ *   dJ/d wavelet[n][s] = sum_corner (w / h^3) mu_{n+1}   (source side),
+ *   dJ/dm = -(1/dt^2) sum_n mu_{n+1} (P u_{n+1} - 2 u_n + Q u_{n-1})
+ * with m = 1/v^2 the squared slowness (the sponge damping is held fixed).
+ */
+
+/*
+ * Keep forward levels for the gradient: allocates a ring of nlevels (>= 3)
+ * wavefield buffers (reused across calls), stores the two current levels,
+ * and from now on every fdw_step stores the level it produces (level l goes
+ * to slot l mod nlevels). A checkpointed gradient restores a segment's start
+ * with fdw_set_wavefield / fdw_set_current_step, calls fdw_history_begin,
+ * replays the segment with fdw_step, then runs the adjoint steps of that
+ * segment. Errors: INVALID_ARG (TTI, nlevels < 3), OOM.
+ */
+int fdw_history_begin(fdw_solver *s, int nlevels);
+int fdw_history_end(fdw_solver *s);
+
+/*
+ * Start an adjoint run: copies the residual [(nt+1)][nrec] FP64 (host or
+ * device), zeroes the multipliers (level k = nt+1) and, when
+ * accumulate_gradient is non-zero, the gradient accumulator. Allocates the
+ * adjoint buffers on first use. Errors: STATE (no dt), INVALID_ARG, OOM.
+ */
+int fdw_adjoint_begin(fdw_solver *s, const double *residual, int nt, int ptr_is_device,
+                      int accumulate_gradient);
+
+/*
+ * Advance the adjoint nsteps levels (k -> k - nsteps, nsteps <= k - 1): the
+ * acoustic stencil kernel on the multiplier buffers, the residual spread,
+ * the source-side adjoint, and (if accumulating) the gradient term of each
+ * produced level, which needs forward levels j, j-1, j-2 in the history
+ * (FDW_ERR_STATE otherwise). Asynchronous on the stream.
+ */
+int fdw_adjoint_step(fdw_solver *s, int nsteps);
+
+/* Current adjoint level k (the multipliers hold mu_k, mu_{k+1}); -1 if none. */
+int fdw_adjoint_current_step(const fdw_solver *s);
+
+/*
+ * dJ/dm on the PHYSICAL grid [nz][ny][nx] FP64 (host or device), m = 1/v^2:
+ * the accumulated sum scaled by -1/dt^2, with the contributions of sponge
+ * points added to the physical point whose medium they copy.
+ * Errors: STATE (no gradient accumulated).
+ */
+int fdw_get_gradient(fdw_solver *s, double *grad_m, int ptr_is_device);
+
+/* dJ/d wavelet [nt][nsrc] FP64 of the adjoint run so far (host or device). */
+int fdw_get_source_adjoint(fdw_solver *s, double *out, int ptr_is_device);
+
+/* Multipliers mu_k (level 0) or mu_{k+1} (level 1), layout of fdw_get_wavefield. */
+int fdw_get_adjoint_wavefield(const fdw_solver *s, int level, float *out, int ptr_is_device);
 
 /*
  * Kernel timing. After fdw_profile_begin, up to max_launches (<= 65536)

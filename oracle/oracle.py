@@ -326,3 +326,19 @@ def acoustic_update_at(u_block, um_c, v_c, gamma_c, h, order, dt):
     um = np.zeros((n, n, n))
     um[r, r, r] = um_c
     return acoustic_step(s, u_block, um)[r, r, r]
+
+
+def extend_adjoint(g, nb):
+    """Adjoint of `extend`: each physical point collects the computational
+    points that copy its value (separable: per axis, the nb sponge slices
+    beyond a face add onto the face slice)."""
+    g = np.asarray(g, dtype=np.float64)
+    if nb == 0:
+        return g.copy()
+    for ax in range(3):
+        a = np.moveaxis(g, ax, 0)
+        inner = a[nb:a.shape[0] - nb].copy()
+        inner[0] += a[:nb].sum(axis=0)
+        inner[-1] += a[a.shape[0] - nb:].sum(axis=0)
+        g = np.moveaxis(inner, 0, ax)
+    return np.ascontiguousarray(g)

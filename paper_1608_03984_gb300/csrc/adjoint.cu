@@ -1,0 +1,104 @@
+// adjoint.cu -- FWI gradient kernels.
+//
+// The paper motivates the solvers by FWI/RTM (Introduction); the gradient
+// is the transpose of the discrete recurrence of Algorithm 1 / Eq. Acou
+// with the sponge. With the forward recurrence
+//   P u_{n+1} = (2 + C L) u_n - Q u_{n-1} + C q_n,   C = dt^2 v^2 = dt^2 / m,
+// and multipliers mu produced by the same step run backwards (fdw_adjoint_*),
+//   dJ/dm = -(1/dt^2) sum_n mu_{n+1} (P u_{n+1} - 2 u_n + Q u_{n-1}).
+// grad_accum adds one term in FP32 (a segment of steps), grad_flush moves
+// the FP32 partial sums into the FP64 total, grad_physical applies the
+// -1/dt^2 scale and the adjoint of the medium's extension into the sponge
+// (each physical point collects every computational point that copies it).
+#include "fdw_internal.h"
+#include "fdwave.h"
+
+namespace fdw {
+
+template <typename T>
+__global__ void grad_accum_kernel(const T *__restrict__ mu, const T *__restrict__ u1,
+                                  const T *__restrict__ u0, const T *__restrict__ um1,
+                                  float *__restrict__ g32, Dims d, Sponge sp) {
+  const size_t n = d.vol();
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
+       p += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(p % d.Xp);
+    if (i >= d.NX) continue;
+    const size_t rest = p / d.Xp;
+    const int j = (int)(rest % d.NY), k = (int)(rest / d.NY);
+    const float gh = sp.gx[i] + sp.gy[j] + sp.gz[k];
+    const float a = St<T>::ld(mu[p]);
+    const float b = (1.f + gh) * St<T>::ld(u1[p]) - 2.f * St<T>::ld(u0[p]) +
+                    (um1 ? (1.f - gh) * St<T>::ld(um1[p]) : 0.f);
+    g32[p] = fmaf(a, b, g32[p]);
+  }
+}
+
+__global__ void grad_flush_kernel(float *__restrict__ g32, double *__restrict__ g64, size_t n) {
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
+       p += (size_t)gridDim.x * blockDim.x) {
+    g64[p] += (double)g32[p];
+    g32[p] = 0.f;
+  }
+}
+
+// out[pk][pj][pi] (physical grid) = scale * sum of g64 over the
+// computational points whose medium is copied from (pi, pj, pk).
+__global__ void grad_physical_kernel(const double *__restrict__ g64, Dims d, int nx, int ny, int nz,
+                                     int nb, double scale, double *__restrict__ out) {
+  const size_t n = (size_t)nx * ny * nz;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int pi = (int)(q % nx);
+    const size_t rest = q / nx;
+    const int pj = (int)(rest % ny), pk = (int)(rest / ny);
+    const int i0 = pi == 0 ? 0 : pi + nb, i1 = pi == nx - 1 ? d.NX - 1 : pi + nb;
+    const int j0 = pj == 0 ? 0 : pj + nb, j1 = pj == ny - 1 ? d.NY - 1 : pj + nb;
+    const int k0 = pk == 0 ? 0 : pk + nb, k1 = pk == nz - 1 ? d.NZ - 1 : pk + nb;
+    double s = 0.0;
+    for (int k = k0; k <= k1; ++k)
+      for (int j = j0; j <= j1; ++j)
+        for (int i = i0; i <= i1; ++i) s += g64[((size_t)k * d.NY + j) * d.Xp + i];
+    out[q] = scale * s;
+  }
+}
+
+static int grid_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
+}
+
+cudaError_t launch_grad_accum(int storage, const void *mu, const void *u1, const void *u0,
+                              const void *um1, float *g32, Dims d, Sponge sp, cudaStream_t st) {
+  switch (storage) {
+    case FDW_F32:
+      grad_accum_kernel<float><<<grid_for(d.vol()), 256, 0, st>>>(
+          (const float *)mu, (const float *)u1, (const float *)u0, (const float *)um1, g32, d, sp);
+      break;
+    case FDW_BF16:
+      grad_accum_kernel<__nv_bfloat16><<<grid_for(d.vol()), 256, 0, st>>>(
+          (const __nv_bfloat16 *)mu, (const __nv_bfloat16 *)u1, (const __nv_bfloat16 *)u0,
+          (const __nv_bfloat16 *)um1, g32, d, sp);
+      break;
+    case FDW_F16:
+      grad_accum_kernel<__half><<<grid_for(d.vol()), 256, 0, st>>>(
+          (const __half *)mu, (const __half *)u1, (const __half *)u0, (const __half *)um1, g32, d, sp);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_flush(float *g32, double *g64, size_t n, cudaStream_t st) {
+  grad_flush_kernel<<<grid_for(n), 256, 0, st>>>(g32, g64, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_physical(const double *g64, Dims d, int nx, int ny, int nz, int nb,
+                                 double scale, double *out, cudaStream_t st) {
+  grad_physical_kernel<<<grid_for((size_t)nx * ny * nz), 256, 0, st>>>(g64, d, nx, ny, nz, nb,
+                                                                       scale, out);
+  return cudaGetLastError();
+}
+
+}  // namespace fdw

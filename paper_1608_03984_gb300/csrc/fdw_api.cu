@@ -62,6 +62,7 @@ struct fdw_solver {
   float *scratch2 = nullptr;  // 4 words: model maxima / flags
   bool model_set = false, dt_set = false;
   double vmax = 0, vmax_eff = 0, dt = 0;
+  double sponge_vref = 0.0, sponge_R = 1e-3;  // vref <= 0: the model's vmax
 
   int nsrc = 0, nt_src = 0;
   int *src_corner = nullptr;
@@ -88,6 +89,27 @@ struct fdw_solver {
   bool prof = false;
   std::vector<cudaEvent_t> ev;
   int prof_n = 0;
+
+  // adjoint (acoustic): multipliers mu_k in a[acur], mu_{k+1} in a[1-acur]
+  void *a[2] = {nullptr, nullptr};
+  int acur = 0;
+  CUtensorMap amap_halo[2], amap_int[2];
+  bool amaps_ok = false;
+  bool adj_on = false, adj_grad = false;
+  int ak = 0;                       // current adjoint level k
+  double *residual = nullptr;       // [(nt_res+1)][nrec]
+  int nt_res = 0;
+  size_t residual_cap = 0;
+  double *src_adj = nullptr;        // [nt_src][nsrc]
+  int *d_astep = nullptr;
+  float *grad32 = nullptr;          // FP32 partial sums of the current segment
+  double *grad64 = nullptr;         // FP64 total (computational grid, unscaled)
+  int grad_pending = 0;             // terms in grad32 not yet flushed
+
+  // forward history ring (levels of u for the gradient)
+  std::vector<void *> hist;
+  std::vector<int> hist_level;
+  bool hist_on = false;
 };
 
 namespace {
@@ -386,6 +408,9 @@ extern "C" int fdw_destroy(fdw_solver *s) {
   dfree(s->src_corner); dfree(s->src_w); dfree(s->wavelet);
   dfree(s->rec_corner); dfree(s->rec_w); dfree(s->traces);
   dfree(s->d_step); dfree(s->d_err);
+  dfree(s->a[0]); dfree(s->a[1]); dfree(s->residual); dfree(s->src_adj); dfree(s->d_astep);
+  dfree(s->grad32); dfree(s->grad64);
+  for (void *p : s->hist) dfree(p);
   if (s->cap) cudaStreamDestroy(s->cap);
   delete s;
   return FDW_OK;
@@ -536,8 +561,9 @@ extern "C" int fdw_set_dt(fdw_solver *s, double dt) {
   s->dt = dt;
   // sponge: gamma_a(i) = gamma_max d(i) / nb, gamma_max = 3 vmax ln(1/R) / (2 nb h), R = 1e-3,
   // d(i) = distance (in points) into the sponge; the tables hold gamma dt / 2.
-  const double R = 1e-3;
-  const double gmax = s->nb > 0 ? 3.0 * s->vmax * log(1.0 / R) / (2.0 * s->nb * s->h) : 0.0;
+  const double R = s->sponge_R;
+  const double vref = s->sponge_vref > 0.0 ? s->sponge_vref : s->vmax;
+  const double gmax = s->nb > 0 ? 3.0 * vref * log(1.0 / R) / (2.0 * s->nb * s->h) : 0.0;
   const int Ns[3] = {s->d.NX, s->d.NY, s->d.NZ};
   const int ns[3] = {s->nx, s->ny, s->nz};
   for (int a = 0; a < 3; ++a) {
@@ -688,6 +714,7 @@ extern "C" int fdw_step(fdw_solver *s, int nsteps) {
   DeviceGuard g(s->device);
   int rc = ensure_graphs(s);
   if (rc) return rc;
+  const size_t fb = s->d.vol() * s->el;
   for (int n = 0; n < nsteps; ++n) {
     if (s->prof && (size_t)(2 * s->prof_n + 1) < s->ev.size()) {
       CK(cudaEventRecord(s->ev[2 * s->prof_n], s->stream));
@@ -701,8 +728,244 @@ extern "C" int fdw_step(fdw_solver *s, int nsteps) {
       CK(cudaGraphLaunch(s->graph[s->cur], s->stream));
     }
     s->cur = 1 - s->cur;
+    if (s->hist_on) {  // keep level it+n+1 for the gradient
+      const int lvl = s->it + n + 1, H = (int)s->hist.size();
+      const int slot = ((lvl % H) + H) % H;
+      CK(cudaMemcpyAsync(s->hist[slot], s->f[0][s->cur], fb, cudaMemcpyDeviceToDevice, s->stream));
+      s->hist_level[slot] = lvl;
+    }
   }
   s->it += nsteps;
+  return FDW_OK;
+}
+
+// --------------------------------------------------------------------------
+// forward history and adjoint (FWI gradient)
+// --------------------------------------------------------------------------
+static int check_err_flag(fdw_solver *s);
+
+static int hist_slot(const fdw_solver *s, int lvl) {
+  const int H = (int)s->hist.size();
+  if (H == 0) return -1;
+  const int slot = ((lvl % H) + H) % H;
+  return s->hist_level[slot] == lvl ? slot : -1;
+}
+
+extern "C" int fdw_history_begin(fdw_solver *s, int nlevels) {
+  if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
+  if (s->eq != FDW_ACOUSTIC) return fail(FDW_ERR_INVALID_ARG, "history/adjoint: acoustic only");
+  if (nlevels < 3) return fail(FDW_ERR_INVALID_ARG, "nlevels must be >= 3");
+  DeviceGuard g(s->device);
+  const size_t fb = s->d.vol() * s->el;
+  while ((int)s->hist.size() < nlevels) {
+    void *p = nullptr;
+    CK(cudaMalloc(&p, fb));
+    s->hist.push_back(p);
+  }
+  while ((int)s->hist.size() > nlevels) {
+    dfree(s->hist.back());
+    s->hist.pop_back();
+  }
+  s->hist_level.assign(s->hist.size(), INT32_MIN);
+  // seed with the two current levels
+  const int H = nlevels;
+  const int l0 = s->it, l1 = s->it - 1;
+  const int s0 = ((l0 % H) + H) % H, s1 = ((l1 % H) + H) % H;
+  CK(cudaMemcpyAsync(s->hist[s0], s->f[0][s->cur], fb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->hist[s1], s->f[0][1 - s->cur], fb, cudaMemcpyDeviceToDevice, s->stream));
+  s->hist_level[s0] = l0;
+  s->hist_level[s1] = l1;
+  s->hist_on = true;
+  return FDW_OK;
+}
+
+extern "C" int fdw_history_end(fdw_solver *s) {
+  if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
+  s->hist_on = false;
+  return FDW_OK;
+}
+
+static int build_adjoint_maps(fdw_solver *s) {
+  if (s->amaps_ok) return FDW_OK;
+  TileGeom tg;
+  if (acoustic_geom(s->storage, s->r, s->tile, &tg)) return fail(FDW_ERR_INVALID_ARG, "bad tile");
+  for (int b = 0; b < 2; ++b) {
+    int rc = make_map(&s->amap_halo[b], s, s->a[b], tg.box_halo_x, tg.box_halo_y);
+    if (rc) return rc;
+    rc = make_map(&s->amap_int[b], s, s->a[b], tg.box_int_x, tg.box_int_y);
+    if (rc) return rc;
+  }
+  s->amaps_ok = true;
+  return FDW_OK;
+}
+
+extern "C" int fdw_adjoint_begin(fdw_solver *s, const double *residual, int nt, int ptr_is_device,
+                                 int accumulate_gradient) {
+  if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
+  if (s->eq != FDW_ACOUSTIC) return fail(FDW_ERR_INVALID_ARG, "adjoint: acoustic only");
+  if (!s->dt_set) return fail(FDW_ERR_STATE, "fdw_set_dt must come before fdw_adjoint_begin");
+  if (nt < 0 || (s->nrec > 0 && !residual)) return fail(FDW_ERR_INVALID_ARG, "bad residual");
+  DeviceGuard g(s->device);
+  const size_t fb = s->d.vol() * s->el;
+  for (int b = 0; b < 2; ++b)
+    if (!s->a[b]) {
+      CK(cudaMalloc(&s->a[b], fb));
+      s->amaps_ok = false;
+    }
+  int rc = build_adjoint_maps(s);
+  if (rc) return rc;
+  if (!s->d_astep) CK(dmalloc(&s->d_astep, sizeof(int)));
+  const size_t rbytes = (size_t)(nt + 1) * (s->nrec > 0 ? s->nrec : 1) * sizeof(double);
+  if (s->residual_cap < rbytes) {
+    dfree(s->residual);
+    s->residual = nullptr;
+    CK(dmalloc(&s->residual, rbytes));
+    s->residual_cap = rbytes;
+  }
+  if (s->nrec > 0) {
+    rc = upload(s->residual, residual, (size_t)(nt + 1) * s->nrec * sizeof(double), ptr_is_device, s->stream);
+    if (rc) return rc;
+  }
+  s->nt_res = nt;
+  dfree(s->src_adj);
+  s->src_adj = nullptr;
+  if (s->nsrc > 0 && s->nt_src > 0) {
+    CK(dmalloc(&s->src_adj, (size_t)s->nt_src * s->nsrc * sizeof(double)));
+    CK(cudaMemsetAsync(s->src_adj, 0, (size_t)s->nt_src * s->nsrc * sizeof(double), s->stream));
+  }
+  for (int b = 0; b < 2; ++b) CK(cudaMemsetAsync(s->a[b], 0, fb, s->stream));
+  s->acur = 0;
+  s->ak = nt + 1;  // mu_{nt+1} = mu_{nt+2} = 0
+  CK(cudaMemcpyAsync(s->d_astep, &s->ak, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+  s->adj_grad = accumulate_gradient != 0;
+  if (s->adj_grad) {
+    if (!s->grad32) CK(dmalloc(&s->grad32, s->d.vol() * sizeof(float)));
+    if (!s->grad64) CK(dmalloc(&s->grad64, s->d.vol() * sizeof(double)));
+    CK(cudaMemsetAsync(s->grad32, 0, s->d.vol() * sizeof(float), s->stream));
+    CK(cudaMemsetAsync(s->grad64, 0, s->d.vol() * sizeof(double), s->stream));
+    s->grad_pending = 0;
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  s->adj_on = true;
+  return FDW_OK;
+}
+
+extern "C" int fdw_adjoint_current_step(const fdw_solver *s) { return s && s->adj_on ? s->ak : -1; }
+
+extern "C" int fdw_adjoint_step(fdw_solver *s, int nsteps) {
+  if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
+  if (!s->adj_on) return fail(FDW_ERR_STATE, "fdw_adjoint_begin must come first");
+  if (nsteps < 0 || nsteps > s->ak - 1)
+    return fail(FDW_ERR_INVALID_ARG, "nsteps must be in [0, %d]", s->ak - 1);
+  DeviceGuard g(s->device);
+  int rc = acoustic_prepare(s->storage, s->r, s->tile) == cudaSuccess ? FDW_OK : FDW_ERR_CUDA;
+  if (rc) return fail(rc, "kernel attribute");
+  for (int n = 0; n < nsteps; ++n) {
+    const int cur = s->acur, nxt = 1 - cur;
+    const int j = s->ak - 1;  // level produced: mu_j
+    AcousticLaunch L{};
+    L.storage = s->storage;
+    L.r = s->r;
+    L.d = s->d;
+    L.w = s->w;
+    L.sp = Sponge{s->gam[0], s->gam[1], s->gam[2]};
+    L.cur = s->a[cur];
+    L.prev = s->a[nxt];
+    L.c = s->c;
+    L.map_cur_halo = &s->amap_halo[cur];
+    L.map_cur_int = &s->amap_int[cur];
+    L.map_prev_int = &s->amap_int[nxt];
+    L.map_c_int = &s->map_c;
+    L.zchunks = s->zchunks;
+    L.err = s->d_err;
+    L.naive = s->naive;
+    L.tile = s->tile;
+    CK(launch_acoustic(L, s->stream));
+    SparseLaunch S{};
+    S.storage = s->storage;
+    S.d = s->d;
+    S.sp = L.sp;
+    S.f0 = s->a[nxt];
+    S.c = s->c;
+    S.nsrc = s->nsrc;
+    S.src_corner = s->src_corner;
+    S.src_w = s->src_w;
+    S.nt_src = s->nt_src;
+    S.nrec = s->nrec;
+    S.rec_corner = s->rec_corner;
+    S.rec_w = s->rec_w;
+    S.step = s->d_astep;
+    S.residual = s->residual;
+    S.nt_res = s->nt_res;
+    S.res_scale = (float)(s->h * s->h);
+    S.adjoint = 1;
+    S.src_adj = s->src_adj;
+    S.src_adj_scale = (float)(1.0 / (s->h * s->h));
+    CK(launch_sparse(S, s->stream));
+    if (s->adj_grad && j >= 1) {
+      // term n = j - 1: mu_j (P u_j - 2 u_{j-1} + Q u_{j-2}), u_{-1} = 0
+      const int s1 = hist_slot(s, j), s0 = hist_slot(s, j - 1), sm = hist_slot(s, j - 2);
+      if (s1 < 0 || s0 < 0 || (sm < 0 && j - 2 >= 0))
+        return fail(FDW_ERR_STATE, "forward levels %d..%d are not in the history", j - 2, j);
+      CK(launch_grad_accum(s->storage, s->a[nxt], s->hist[s1], s->hist[s0],
+                           sm >= 0 ? s->hist[sm] : nullptr, s->grad32, s->d, L.sp, s->stream));
+      if (++s->grad_pending >= 64) {
+        CK(launch_grad_flush(s->grad32, s->grad64, s->d.vol(), s->stream));
+        s->grad_pending = 0;
+      }
+    }
+    s->acur = nxt;
+    s->ak = j;
+  }
+  return FDW_OK;
+}
+
+extern "C" int fdw_get_gradient(fdw_solver *s, double *grad_m, int ptr_is_device) {
+  if (!s || !grad_m) return fail(FDW_ERR_INVALID_ARG, "NULL solver or output");
+  if (!s->adj_on || !s->adj_grad) return fail(FDW_ERR_STATE, "no gradient is being accumulated");
+  DeviceGuard g(s->device);
+  CK(launch_grad_flush(s->grad32, s->grad64, s->d.vol(), s->stream));
+  s->grad_pending = 0;
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  double *dst = grad_m;
+  if (!ptr_is_device) CK(dmalloc(&dst, n * sizeof(double)));
+  cudaError_t e = launch_grad_physical(s->grad64, s->d, s->nx, s->ny, s->nz, s->nb,
+                                       -1.0 / (s->dt * s->dt), dst, s->stream);
+  if (e == cudaSuccess && !ptr_is_device) {
+    e = cudaMemcpyAsync(grad_m, dst, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(dst);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "fdw_get_gradient");
+  return ptr_is_device ? FDW_OK : check_err_flag(s);
+}
+
+extern "C" int fdw_get_source_adjoint(fdw_solver *s, double *out, int ptr_is_device) {
+  if (!s || !out) return fail(FDW_ERR_INVALID_ARG, "NULL solver or output");
+  if (!s->adj_on || !s->src_adj) return fail(FDW_ERR_STATE, "no source adjoint (no sources or no adjoint run)");
+  DeviceGuard g(s->device);
+  const size_t bytes = (size_t)s->nt_src * s->nsrc * sizeof(double);
+  CK(cudaMemcpyAsync(out, s->src_adj, bytes, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     s->stream));
+  if (!ptr_is_device) return check_err_flag(s);
+  return FDW_OK;
+}
+
+extern "C" int fdw_get_adjoint_wavefield(const fdw_solver *cs, int level, float *out, int ptr_is_device) {
+  fdw_solver *s = (fdw_solver *)cs;
+  if (!s || !out || level < 0 || level > 1) return fail(FDW_ERR_INVALID_ARG, "bad arguments");
+  if (!s->adj_on) return fail(FDW_ERR_STATE, "no adjoint run");
+  DeviceGuard g(s->device);
+  const size_t n = (size_t)s->d.NX * s->d.NY * s->d.NZ;
+  float *dst = out;
+  if (!ptr_is_device) CK(dmalloc(&dst, n * sizeof(float)));
+  cudaError_t e = launch_unpack(s->storage, s->a[level == 0 ? s->acur : 1 - s->acur], s->d, dst, s->stream);
+  if (e == cudaSuccess && !ptr_is_device) {
+    e = cudaMemcpyAsync(out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(dst);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "fdw_get_adjoint_wavefield");
   return FDW_OK;
 }
 
@@ -831,6 +1094,16 @@ extern "C" int fdw_check(fdw_solver *s, int check_finite) {
     CK(cudaStreamSynchronize(s->stream));
     if (flag) return fail(FDW_ERR_DIVERGED, "non-finite values in the wavefield at step %d", s->it);
   }
+  return FDW_OK;
+}
+
+extern "C" int fdw_set_sponge(fdw_solver *s, double vref, double R) {
+  if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
+  if (!isfinite(vref) || !(R > 0.0 && R < 1.0)) return fail(FDW_ERR_INVALID_ARG, "need finite vref, 0 < R < 1");
+  s->sponge_vref = vref;
+  s->sponge_R = R;
+  s->dt_set = false;
+  drop_graphs(s);
   return FDW_OK;
 }
 

@@ -157,8 +157,17 @@ struct SparseLaunch {
   int nt_res;
   float res_scale;           // h^2: c' = c / h^2 is stored, the adjoint source is c R^T res
   int adjoint;
+  double *src_adj;           // [nt_src][nsrc] adjoint w.r.t. the wavelet, or null
+  float src_adj_scale;       // 1 / h^2
 };
 cudaError_t launch_sparse(const SparseLaunch &L, cudaStream_t st);
+
+// FWI gradient kernels (adjoint.cu)
+cudaError_t launch_grad_accum(int storage, const void *mu, const void *u1, const void *u0,
+                              const void *um1, float *g32, Dims d, Sponge sp, cudaStream_t st);
+cudaError_t launch_grad_flush(float *g32, double *g64, size_t n, cudaStream_t st);
+cudaError_t launch_grad_physical(const double *g64, Dims d, int nx, int ny, int nz, int nb,
+                                 double scale, double *out, cudaStream_t st);
 
 // Utility kernels (setup.cu)
 cudaError_t launch_coef_acoustic(int storage, const float *vp_phys, int nx, int ny, int nz,

@@ -53,17 +53,34 @@ __global__ void __launch_bounds__(256) inject_kernel(SparseLaunch L) {
     // receiver weights (no 1/h^3), scaled like the stencil term:
     // dt^2 v^2 w res / P = c' h^2 w res / P.
     const int k = n - 1;
-    if (k < 0 || k > L.nt_res || !L.residual) return;
-    for (int t = threadIdx.x; t < L.nrec * 8; t += blockDim.x) {
-      const float wt = L.rec_w[t];
-      if (wt == 0.f) continue;
-      const int s = t >> 3;
-      const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], kk = L.rec_corner[t * 3 + 2];
-      const size_t p = (size_t)kk * plane + (size_t)j * L.d.Xp + i;
-      const float res = (float)L.residual[(size_t)k * L.nrec + s];
-      const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[kk];
-      const float cc = St<T>::ld(((const T *)L.c)[p]);
-      atomic_add_st<T>((T *)L.f0 + p, cc * L.res_scale * wt * res * __frcp_rn(1.f + gh));
+    if (k < 0) return;
+    if (k <= L.nt_res && L.residual) {
+      for (int t = threadIdx.x; t < L.nrec * 8; t += blockDim.x) {
+        const float wt = L.rec_w[t];
+        if (wt == 0.f) continue;
+        const int s = t >> 3;
+        const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], kk = L.rec_corner[t * 3 + 2];
+        const size_t p = (size_t)kk * plane + (size_t)j * L.d.Xp + i;
+        const float res = (float)L.residual[(size_t)k * L.nrec + s];
+        const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[kk];
+        const float cc = St<T>::ld(((const T *)L.c)[p]);
+        atomic_add_st<T>((T *)L.f0 + p, cc * L.res_scale * wt * res * __frcp_rn(1.f + gh));
+      }
+    }
+    // Source side of the adjoint: d J / d wavelet[k-1][s] = sum_corner w / h^3 mu_k
+    // (the stored source weights are w / h; src_adj_scale = 1 / h^2).
+    if (L.src_adj && k >= 1 && k - 1 < L.nt_src) {
+      __syncthreads();  // the spread above is visible to the whole block
+      for (int s = threadIdx.x; s < L.nsrc; s += blockDim.x) {
+        double acc = 0.0;
+        for (int q = 0; q < 8; ++q) {
+          const int t = s * 8 + q;
+          const int i = L.src_corner[t * 3 + 0], j = L.src_corner[t * 3 + 1], kk = L.src_corner[t * 3 + 2];
+          const float v = St<T>::ld(((const T *)L.f0)[(size_t)kk * plane + (size_t)j * L.d.Xp + i]);
+          acc += (double)L.src_w[t] * (double)v;
+        }
+        L.src_adj[(size_t)(k - 1) * L.nsrc + s] = acc * (double)L.src_adj_scale;
+      }
     }
   }
 }

@@ -54,6 +54,15 @@ _SIGS = {
     "fdw_get_zchunks": ([_P], _I),
     "fdw_set_tile_config": ([_P, _I], _I),
     "fdw_get_tile_config": ([_P], _I),
+    "fdw_set_sponge": ([_P, _D, _D], _I),
+    "fdw_history_begin": ([_P, _I], _I),
+    "fdw_history_end": ([_P], _I),
+    "fdw_adjoint_begin": ([_P, _P, _I, _I, _I], _I),
+    "fdw_adjoint_step": ([_P, _I], _I),
+    "fdw_adjoint_current_step": ([_P], _I),
+    "fdw_get_gradient": ([_P, _P, _I], _I),
+    "fdw_get_source_adjoint": ([_P, _P, _I], _I),
+    "fdw_get_adjoint_wavefield": ([_P, _I, _P, _I], _I),
     "fdw_profile_begin": ([_P, _I], _I),
     "fdw_profile_end": ([_P, ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
 }
@@ -186,6 +195,11 @@ class Solver:
         _chk(lib().fdw_set_model(self._h, *[p[0] for p in ptrs], dev))
         return self
 
+    def set_sponge(self, vref=0.0, R=1e-3):
+        """Fix the sponge's velocity scale (vref <= 0: the model's vmax)."""
+        _chk(lib().fdw_set_sponge(self._h, float(vref), float(R)))
+        return self
+
     def max_stable_dt(self):
         return lib().fdw_max_stable_dt(self._h)
 
@@ -271,6 +285,45 @@ class Solver:
     @property
     def zchunks(self):
         return lib().fdw_get_zchunks(self._h)
+
+    # -- adjoint / FWI gradient --------------------------------------------
+    def history_begin(self, nlevels):
+        _chk(lib().fdw_history_begin(self._h, int(nlevels)))
+
+    def history_end(self):
+        _chk(lib().fdw_history_end(self._h))
+
+    def adjoint_begin(self, residual, gradient=True):
+        """residual: [(nt+1), nrec] float64 (numpy or torch, host or device)."""
+        p, dev, keep = _ptr(residual, np.float64)
+        n = keep.shape[0] - 1
+        self._res_keep = keep
+        _chk(lib().fdw_adjoint_begin(self._h, p, int(n), dev, int(bool(gradient))))
+
+    def adjoint_step(self, n=1):
+        _chk(lib().fdw_adjoint_step(self._h, int(n)))
+
+    @property
+    def adjoint_current_step(self):
+        return lib().fdw_adjoint_current_step(self._h)
+
+    def gradient(self, out=None):
+        """dJ/dm (m = 1/v^2) on the physical grid, float64."""
+        if out is None:
+            out = np.zeros(self.shape, dtype=np.float64)
+        p, dev, keep = _ptr(out, np.float64)
+        _chk(lib().fdw_get_gradient(self._h, p, dev))
+        return keep if not _is_torch(out) or keep is out else out.copy_(keep)
+
+    def source_adjoint(self, nt, nsrc):
+        out = np.zeros((nt, nsrc), dtype=np.float64)
+        _chk(lib().fdw_get_source_adjoint(self._h, out.ctypes.data, 0))
+        return out
+
+    def adjoint_wavefield(self, level=0):
+        out = np.zeros(self.comp_shape, dtype=np.float32)
+        _chk(lib().fdw_get_adjoint_wavefield(self._h, int(level), out.ctypes.data, 0))
+        return out
 
     def profile_begin(self, max_launches=65536):
         _chk(lib().fdw_profile_begin(self._h, int(max_launches)))
