@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--tile", type=int, default=-1, help="2.5D kernel tile configuration (-1 default)")
     p.add_argument("--zchunks", type=int, default=0, help="CTAs along z (0 default)")
     p.add_argument("--no-tti", action="store_true")
+    p.add_argument("--no-fwi", action="store_true")
+    p.add_argument("--fwi-n", type=int, default=256)
+    p.add_argument("--fwi-nt", type=int, default=2000)
+    p.add_argument("--fwi-shots-side", type=int, default=4)
     p.add_argument("--tti-n", type=int, default=384, help="physical TTI grid points per axis")
     return p.parse_args()
 
@@ -70,24 +74,28 @@ def peaks():
 
 
 def kernel_source_sha():
+    """Hash of the acoustic stencil kernel's source (template + dispatch + PTX helpers)."""
     h = hashlib.sha256()
-    for f in ("acoustic.cu", "acoustic_kernel.cuh", "ptx.cuh", "fdw_internal.h"):
+    for f in ("acoustic.cu", "acoustic_kernel.cuh", "ptx.cuh"):
         with open(os.path.join(ROOT, "paper_1608_03984_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic_per_point():
-    """DRAM bytes per point of the stencil kernel from the committed ncu
-    summary, if its kernel-source hash matches the current source."""
-    path = os.path.join(ROOT, "profiles", "acoustic_step_592_ncu.md")
+    """{order: DRAM bytes per point} of the stencil kernel at 592^3 from the
+    committed ncu summary, if its kernel-source hash matches the source."""
+    path = os.path.join(ROOT, "profiles", "acoustic_step_592_dram.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"TRAFFIC_BYTES_PER_POINT\s+([0-9.]+)\s+source_sha=([0-9a-f]+)", text)
-    if not m or m.group(2) != kernel_source_sha():
+    m = re.search(r"source_sha=([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_source_sha():
         return None
-    return float(m.group(1))
+    out = {}
+    for o, v in re.findall(r"TRAFFIC_BYTES_PER_POINT order=(\d+) ([0-9.]+)", text):
+        out[int(o)] = float(v)
+    return out or None
 
 
 class ClockSampler:
@@ -320,10 +328,15 @@ def run_fdwave(args, orders):
         sum_kms += kms
     achieved = sum_bytes / (sum_kms / 1e3) / 1e9
     tpp = ncu_traffic_per_point()
+    traffic = None
+    if tpp is not None and all(o in tpp for o in orders):
+        # mean DRAM bytes per launch over the orders of the sweep (ncu, 592^3)
+        traffic = sum(tpp[o] for o in orders) / len(orders) * points
+        for o in orders:
+            per_order[str(o)]["ncu_dram_bytes_per_point"] = tpp[o]
     roof = {"kernel": "acoustic_tma_kernel (orders %s)" % "/".join(map(str, orders)),
             "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "peak_source": peak_src,
-            "traffic": None if tpp is None else tpp * points,
+            "frac": achieved / hbm, "peak_source": peak_src, "traffic": traffic,
             "algorithmic_bytes_per_launch": BYTES_PER_POINT * points}
 
     e2e = None
@@ -334,6 +347,9 @@ def run_fdwave(args, orders):
     tti = None
     if not args.no_tti:
         tti = run_tti(args, stream, steps=min(args.steps, 30), warmup=3)
+    fwi_res = None
+    if not args.no_fwi and world == 1:
+        fwi_res = run_fwi(args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -352,6 +368,7 @@ def run_fdwave(args, orders):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_dict(args, orders, base),
             "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu, "tti": tti,
+            "fwi": fwi_res,
             "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
         }
         print(json.dumps(line), flush=True)
@@ -395,6 +412,39 @@ def run_tti(args, stream, steps, warmup):
                 "kernel_ms": avg, "gpts": gpts, "achieved_gbs": gpts * bpp,
                 "frac_of_measured_hbm": gpts * bpp / hbm}
     return out
+
+
+def run_fwi(args):
+    """FWI gradient wall time: 256^3 + 40-point sponge (336^3), h = 15 m,
+    order 8, 2000 steps, 4 x 4 shots, 128 x 128 receivers, 20 checkpoints
+    per shot: observed data from the true model (untimed), then the misfit
+    and its velocity gradient for all shots from the starting model (timed:
+    forward runs, checkpoint replays, adjoint runs, gradient reductions)."""
+    import torch
+    from paper_1608_03984_gb300 import fwi, synth
+    w = synth.fwi(n=args.fwi_n, nt=args.fwi_nt, shots_side=args.fwi_shots_side)
+    vref = 1.1 * float(max(w.v_true.max(), w.v_start.max()))
+    sv = fwi.Survey(w.n, w.h, w.nb, w.order, w.dt, w.nt, w.src_xyz, w.wavelet, w.rec_xyz,
+                    checkpoints=w.checkpoints, sponge_vref=vref)
+    with torch.no_grad():
+        d_obs = fwi.fwi_traces(torch.from_numpy(w.v_true).cuda(), sv)
+    v0 = torch.from_numpy(w.v_start).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, g = fwi.misfit_and_gradient(v0, sv, d_obs)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    nz, ny, nx = (k + 2 * w.nb for k in w.n)
+    pts = nz * ny * nx
+    nshot = sv.nshot
+    # stencil steps per shot: forward + replay + adjoint
+    return {"workload": "fwi %d^3 + %d-point sponge (%d^3), h=15 m, order 8, %d steps, %d shots, "
+                        "%d receivers, %d checkpoints/shot" % (w.n[0], w.nb, nz, w.nt, nshot,
+                                                                w.rec_xyz.shape[0], w.checkpoints),
+            "gradient_s": sec, "per_shot_s": sec / nshot, "misfit": float(J),
+            "stencil_steps": 3 * w.nt * nshot,
+            "gpts_equiv": 3 * w.nt * nshot * pts / sec / 1e9,
+            "gradient_finite": bool(torch.isfinite(g).all())}
 
 
 def run_e2e(args, orders, base, stream):

@@ -49,28 +49,13 @@ __global__ void __launch_bounds__(256) inject_kernel(SparseLaunch L) {
       if (L.f1) atomic_add_st<T>((T *)L.f1 + p, v);
     }
   } else {
-    // Adjoint step producing level k = n - 1: spread residual row k with the
-    // receiver weights (no 1/h^3), scaled like the stencil term:
-    // dt^2 v^2 w res / P = c' h^2 w res / P.
+    // Adjoint step that produced level k = n - 1 (the residual was spread by
+    // adjoint_spread_kernel just before). Source side of the adjoint:
+    // d J / d wavelet[k-1][s] = sum_corner w / h^3 mu_k (the stored source
+    // weights are w / h; src_adj_scale = 1 / h^2).
     const int k = n - 1;
     if (k < 0) return;
-    if (k <= L.nt_res && L.residual) {
-      for (int t = threadIdx.x; t < L.nrec * 8; t += blockDim.x) {
-        const float wt = L.rec_w[t];
-        if (wt == 0.f) continue;
-        const int s = t >> 3;
-        const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], kk = L.rec_corner[t * 3 + 2];
-        const size_t p = (size_t)kk * plane + (size_t)j * L.d.Xp + i;
-        const float res = (float)L.residual[(size_t)k * L.nrec + s];
-        const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[kk];
-        const float cc = St<T>::ld(((const T *)L.c)[p]);
-        atomic_add_st<T>((T *)L.f0 + p, cc * L.res_scale * wt * res * __frcp_rn(1.f + gh));
-      }
-    }
-    // Source side of the adjoint: d J / d wavelet[k-1][s] = sum_corner w / h^3 mu_k
-    // (the stored source weights are w / h; src_adj_scale = 1 / h^2).
     if (L.src_adj && k >= 1 && k - 1 < L.nt_src) {
-      __syncthreads();  // the spread above is visible to the whole block
       for (int s = threadIdx.x; s < L.nsrc; s += blockDim.x) {
         double acc = 0.0;
         for (int q = 0; q < 8; ++q) {
@@ -105,10 +90,36 @@ __global__ void __launch_bounds__(256) gather_kernel(SparseLaunch L) {
   L.traces[(size_t)n1 * L.nrec + r] = acc;
 }
 
+// Adjoint step producing level k = *step - 1 (the counter is decremented by
+// the injection kernel that follows): spread residual row k with the
+// receiver weights (no 1/h^3), scaled like the stencil term,
+// dt^2 v^2 w res / P = c' h^2 w res / P. One thread per receiver corner.
+template <typename T>
+__global__ void __launch_bounds__(256) adjoint_spread_kernel(SparseLaunch L) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.nrec * 8) return;
+  const int k = *L.step - 1;
+  if (k < 0 || k > L.nt_res) return;
+  const float wt = L.rec_w[t];
+  if (wt == 0.f) return;
+  const int s = t >> 3;
+  const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], kk = L.rec_corner[t * 3 + 2];
+  const size_t p = (size_t)kk * L.d.plane() + (size_t)j * L.d.Xp + i;
+  const float res = (float)L.residual[(size_t)k * L.nrec + s];
+  const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[kk];
+  const float cc = St<T>::ld(((const T *)L.c)[p]);
+  atomic_add_st<T>((T *)L.f0 + p, cc * L.res_scale * wt * res * __frcp_rn(1.f + gh));
+}
+
 template <typename T>
 static cudaError_t launch_sparse_t(const SparseLaunch &L, cudaStream_t st) {
+  cudaError_t e;
+  if (L.adjoint && L.residual && L.nrec > 0) {
+    adjoint_spread_kernel<T><<<(L.nrec * 8 + 255) / 256, 256, 0, st>>>(L);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   inject_kernel<T><<<1, 256, 0, st>>>(L);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (!L.adjoint && L.nrec > 0 && L.traces) {
     gather_kernel<T><<<(L.nrec + 255) / 256, 256, 0, st>>>(L);

@@ -188,6 +188,72 @@ def random_tti(n: int = 384, h: float = 12.5, nb: int = 40, order: int = 8, nt: 
                     eps=f32(eps), delta=f32(delta), theta=f32(theta), phi=f32(phi), f0=f0)
 
 
+def gaussian_smooth(a: np.ndarray, sigma_pts: float) -> np.ndarray:
+    """Periodic Gaussian smoothing (FFT) of a 3D array, edge-padded by
+    3 sigma first so the model's faces do not wrap into each other."""
+    pad = int(min(3 * sigma_pts, max(a.shape)))
+    b = np.pad(np.asarray(a, np.float64), pad, mode="edge")
+    B = np.fft.rfftn(b)
+    kz = np.fft.fftfreq(b.shape[0])[:, None, None]
+    ky = np.fft.fftfreq(b.shape[1])[None, :, None]
+    kx = np.fft.rfftfreq(b.shape[2])[None, None, :]
+    B *= np.exp(-2.0 * (math.pi * sigma_pts) ** 2 * (kx * kx + ky * ky + kz * kz))
+    out = np.fft.irfftn(B, s=b.shape, axes=(0, 1, 2))
+    return out[pad:pad + a.shape[0], pad:pad + a.shape[1], pad:pad + a.shape[2]]
+
+
+@dataclasses.dataclass
+class FwiWorkload:
+    n: tuple
+    h: float
+    nb: int
+    order: int
+    dt: float
+    nt: int
+    v_true: np.ndarray
+    v_start: np.ndarray
+    src_xyz: np.ndarray      # (nshot, 3)
+    wavelet: np.ndarray      # (nt,)
+    rec_xyz: np.ndarray      # (nrec, 3)
+    checkpoints: int = 20
+
+
+def fwi(n: int = 256, h: float = 15.0, nb: int = 40, order: int = 8, nt: int = 2000,
+        shots_side: int = 4, rec_side: int = 128, f0: float = 8.0, checkpoints: int = 20,
+        seed: int | None = None) -> FwiWorkload:
+    """FWI workload (256^3, h = 15 m): true model = smooth random velocity
+    (correlation length 200 m) plus three Gaussian anomalies of +-10%
+    (sigma 150 m, seeded centres); starting model = the true one smoothed
+    with sigma = 40 points; 4 x 4 shots at 30 m depth over the middle half,
+    128 x 128 receivers at 30 m depth, Ricker 8 Hz, dt at CFL 0.4 of the
+    largest velocity."""
+    seed = SEED_BASE["fwi"] if seed is None else seed
+    shp = (n, n, n)
+    v = random_velocity(shp, h, 200.0, seed).astype(np.float64)
+    r = rng(seed + 1)
+    zz, yy, xx = (np.arange(k, dtype=np.float64) * h for k in shp)
+    sig = 150.0
+    for sign in (1.0, -1.0, 1.0):
+        c = r.uniform(0.25, 0.75, size=3) * (n - 1) * h
+        g = (np.exp(-((zz - c[0]) ** 2) / (2 * sig * sig))[:, None, None]
+             * np.exp(-((yy - c[1]) ** 2) / (2 * sig * sig))[None, :, None]
+             * np.exp(-((xx - c[2]) ** 2) / (2 * sig * sig))[None, None, :])
+        v *= 1.0 + sign * 0.1 * g
+    v_true = v.astype(np.float32)
+    v_start = gaussian_smooth(v, 40.0).astype(np.float32)
+    vmax = max(float(v_true.max()), float(v_start.max()))
+    dt = _cfl_dt(h, vmax)
+    span = (n - 1) * h
+    s = np.linspace(0.25 * span, 0.75 * span, shots_side)
+    SX, SY = np.meshgrid(s, s, indexing="xy")
+    src = np.stack([SX.ravel(), SY.ravel(), np.full(SX.size, 30.0)], axis=1)
+    g = np.linspace(0.0, span, rec_side)
+    RX, RY = np.meshgrid(g, g, indexing="xy")
+    rec = np.stack([RX.ravel(), RY.ravel(), np.full(RX.size, 30.0)], axis=1)
+    w = ricker(f0, dt, nt).astype(np.float32)
+    return FwiWorkload(shp, h, nb, order, dt, nt, v_true, v_start, src, w, rec, checkpoints)
+
+
 def random_wavefield(shape, seed, scale=1.0, smooth_pts=2.0):
     """Smooth random field used as a wavefield state for one-step checks."""
     return (scale * smooth_random_field(shape, smooth_pts, seed)).astype(np.float32)
