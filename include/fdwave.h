@@ -259,6 +259,21 @@ int fdw_get_gradient(fdw_solver *s, double *grad_m, int ptr_is_device);
 /* dJ/d wavelet [nt][nsrc] FP64 of the adjoint run so far (host or device). */
 int fdw_get_source_adjoint(fdw_solver *s, double *out, int ptr_is_device);
 
+/*
+ * FWI data misfit of traces d against observations d_obs (both n FP64
+ * values in device memory): residual[i] = d[i] - d_obs[i] (skipped when
+ * residual is NULL; it is the residual fdw_adjoint_begin takes) and
+ * *J = 1/2 sum residual^2 (FP64, device memory). Deterministic: the sum is
+ * taken over fixed chunks of 2048 values, then over the chunk sums in a
+ * fixed order. Asynchronous on `stream` (a cudaStream_t or NULL); the chunk
+ * sums live in a scratch buffer taken from the stream-ordered allocator
+ * (cudaMallocAsync) and returned at the end of the call.
+ * d and d_obs may be NULL when n = 0 (then *J = 0).
+ * Errors: INVALID_ARG (NULL pointers, n < 0), OOM, CUDA.
+ */
+int fdw_misfit(const double *d, const double *d_obs, long long n, double *residual, double *J,
+               void *stream);
+
 /* Multipliers mu_k (level 0) or mu_{k+1} (level 1), layout of fdw_get_wavefield. */
 int fdw_get_adjoint_wavefield(const fdw_solver *s, int level, float *out, int ptr_is_device);
 

@@ -77,5 +77,5 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
                 extra_flags=["-Xptxas", "-v"] if "--ptxas" in sys.argv else []))

@@ -27,6 +27,15 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
+// Error reporting for the other translation units of the library.
+int fdw::report_error(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return code;
+}
+
 static int cuda_fail(cudaError_t e, const char *what) {
   cudaGetLastError();  // clear a non-sticky error
   return fail(e == cudaErrorMemoryAllocation ? FDW_ERR_OOM : FDW_ERR_CUDA, "%s: %s", what,

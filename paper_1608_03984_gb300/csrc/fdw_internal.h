@@ -162,6 +162,9 @@ struct SparseLaunch {
 };
 cudaError_t launch_sparse(const SparseLaunch &L, cudaStream_t st);
 
+// Set the thread-local message of fdw_last_error and return `code`.
+int report_error(int code, const char *fmt, ...);
+
 // FWI gradient kernels (adjoint.cu)
 cudaError_t launch_grad_accum(int storage, const void *mu, const void *u1, const void *u0,
                               const void *um1, float *g32, Dims d, Sponge sp, cudaStream_t st);

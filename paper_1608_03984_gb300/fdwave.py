@@ -63,6 +63,7 @@ _SIGS = {
     "fdw_get_gradient": ([_P, _P, _I], _I),
     "fdw_get_source_adjoint": ([_P, _P, _I], _I),
     "fdw_get_adjoint_wavefield": ([_P, _I, _P, _I], _I),
+    "fdw_misfit": ([_P, _P, ctypes.c_longlong, _P, _P, _P], _I),
     "fdw_profile_begin": ([_P, _I], _I),
     "fdw_profile_end": ([_P, ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
 }
@@ -144,6 +145,29 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def _cuda_f64(t, name):
+    import torch
+    if not (_is_torch(t) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    return t.data_ptr()
+
+
+def misfit(d, d_obs, residual=None, J=None, stream=None):
+    """Residual d - d_obs (into `residual` if given) and J = 1/2 sum r^2 by
+    fdw_misfit; d, d_obs, residual, J are float64 CUDA tensors. Returns J
+    (a 0-d CUDA tensor), asynchronous on the stream."""
+    import torch
+    n = d.numel()
+    if d_obs.numel() != n or (residual is not None and residual.numel() != n):
+        raise ValueError("size mismatch")
+    if J is None:
+        J = torch.empty((), dtype=torch.float64, device=d.device)
+    rp = _cuda_f64(residual, "residual") if residual is not None else None
+    _chk(lib().fdw_misfit(_cuda_f64(d, "d"), _cuda_f64(d_obs, "d_obs"), n, rp,
+                          _cuda_f64(J, "J"), _stream_handle(stream)))
+    return J
 
 
 class Solver:

@@ -137,9 +137,22 @@ def fwi_traces(vp, survey: Survey):
 
 
 def misfit_and_gradient(vp, survey: Survey, d_obs):
-    """J = 1/2 sum (F(vp) - d_obs)^2 over shots and its gradient dJ/dvp."""
-    v = vp.detach().clone().requires_grad_(True)
-    tr = fwi_traces(v, survey)
-    J = 0.5 * torch.sum((tr - d_obs) ** 2)
-    J.backward()
-    return J.detach(), v.grad
+    """J = 1/2 sum (F(vp) - d_obs)^2 over shots and its gradient dJ/dvp,
+    shot by shot (forward with checkpoints, residual and misfit by
+    fdw_misfit, adjoint with checkpoint replay), so only one shot's
+    checkpoints are held at a time."""
+    eng = _Engine(survey)
+    eng.set_model(vp.detach().float().contiguous())
+    J = torch.zeros((), dtype=torch.float64, device="cuda")
+    Jk = torch.empty_like(J)
+    gm = torch.zeros(vp.shape, dtype=torch.float64, device="cuda")
+    for k in range(survey.nshot):
+        tr, ck = eng.forward_shot(k, keep=True)
+        res = torch.empty_like(tr)
+        fdwave.misfit(tr, d_obs[k].contiguous(), residual=res, J=Jk)
+        J += Jk
+        gm += eng.adjoint_shot(k, res, ck)
+        del ck
+    eng.close()
+    v = vp.detach().double()
+    return J, (gm * (-2.0 / v ** 3)).to(vp.dtype)

@@ -152,6 +152,12 @@ def test_fwi_autograd_finite_differences(fdw):
     v = torch.from_numpy(v0).cuda()
     J0, g = fwi.misfit_and_gradient(v, survey, d_obs)
     assert torch.isfinite(g).all() and float(J0) > 0
+    # the torch.autograd path (FwiTraces + a torch loss) gives the same gradient
+    va = v.clone().requires_grad_(True)
+    Ja = 0.5 * torch.sum((fwi.fwi_traces(va, survey) - d_obs) ** 2)
+    Ja.backward()
+    assert abs(float(Ja) - float(J0)) <= 1e-9 * float(J0)
+    assert float((va.grad - g).norm() / g.norm()) <= 1e-5
 
     def J(vv):
         with torch.no_grad():
@@ -178,3 +184,23 @@ def test_fwi_autograd_finite_differences(fdw):
         big += abs(lin) > 1e-2 * scale
     assert max(errs) < 2e-2, errs
     assert big >= 5
+
+
+@pytest.mark.parametrize("n", [0, 1, 2047, 2048, 2049, 1_000_003])
+def test_misfit_matches_numpy_and_is_deterministic(fdw, n):
+    """fdw_misfit: residual d - d_obs exactly, J = 1/2 sum r^2 to FP64
+    rounding, and the same bits on every call."""
+    import torch
+    rng = np.random.default_rng(n)
+    d = rng.standard_normal(n)
+    o = rng.standard_normal(n)
+    dt, ot = torch.from_numpy(d).cuda(), torch.from_numpy(o).cuda()
+    res = torch.empty_like(dt)
+    J1 = float(fdw.misfit(dt, ot, residual=res))
+    J2 = float(fdw.misfit(dt, ot))
+    np.testing.assert_array_equal(res.cpu().numpy(), d - o)
+    exp = 0.5 * float(np.sum((d - o) ** 2))
+    assert J1 == J2
+    assert abs(J1 - exp) <= 1e-12 * max(exp, 1e-300)
+    with pytest.raises(ValueError):
+        fdw.misfit(dt.float(), ot)
