@@ -274,6 +274,31 @@ int fdw_get_source_adjoint(fdw_solver *s, double *out, int ptr_is_device);
 int fdw_misfit(const double *d, const double *d_obs, long long n, double *residual, double *J,
                void *stream);
 
+/*
+ * fdw_misfit without any device allocation. The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * themselves or have the library do it -- code that owns every byte of the
+ * GPU through its own pool allocator, a real-time loop that cannot afford
+ * the implicit synchronisation of cudaMalloc / cudaFree, or a process close
+ * to running out of device memory.
+ * Same arguments, results and determinism as fdw_misfit (the caller still
+ * passes the inputs d, d_obs and the outputs residual, J in device memory),
+ * but the chunk sums go to a scratch array compiled into the library: 256 KB
+ * per GPU, held from the first use until the process exits. Limit:
+ * n <= 67,108,864 values (32,768 chunks of 2048); larger n returns
+ * FDW_ERR_INVALID_ARG with a message naming the limit.
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current); make that first call before capturing the
+ * stream into a CUDA graph. Every call, from any stream or thread, shares
+ * the one scratch array of the device: calls that overlap on the GPU race
+ * and must be serialised by the caller (e.g. issue them on one stream).
+ * Nothing in the scratch needs clearing between calls (every chunk sum a
+ * call reads, that call writes first).
+ * Errors: INVALID_ARG (NULL pointers, n < 0, n above the limit), CUDA.
+ */
+int fdw_misfit_noalloc(const double *d, const double *d_obs, long long n, double *residual,
+                       double *J, void *stream);
+
 /* Multipliers mu_k (level 0) or mu_{k+1} (level 1), layout of fdw_get_wavefield. */
 int fdw_get_adjoint_wavefield(const fdw_solver *s, int level, float *out, int ptr_is_device);
 

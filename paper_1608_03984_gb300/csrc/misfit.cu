@@ -7,6 +7,8 @@
 // result does not depend on the launch or on other work on the GPU.
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fdw_internal.h"
 #include "fdwave.h"
 
@@ -71,6 +73,62 @@ cudaError_t launch_misfit(const double *d, const double *o, long long n, double 
 }  // namespace fdw
 
 using namespace fdw;
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant. Its chunk sums live in this file-scope device
+// array (256 KB on every GPU that loads the library, kept until the process
+// exits) instead of memory taken per call. Host code cannot use the
+// array's name as a device address: the address is looked up once per
+// device with cudaGetSymbolAddress and cached below.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr long long kNoAllocChunks = 32768;
+constexpr long long kNoAllocMaxValues = kNoAllocChunks * fdw::kMisfitChunk;  // 67,108,864
+static __device__ __align__(256) double g_misfit_scratch[kNoAllocChunks];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double *g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" int fdw_misfit_noalloc(const double *d, const double *d_obs, long long n,
+                                  double *residual, double *J, void *stream) {
+  if ((n > 0 && (!d || !d_obs)) || !J || n < 0)
+    return report_error(FDW_ERR_INVALID_ARG, "fdw_misfit_noalloc: NULL pointer or n < 0");
+  if (n > kNoAllocMaxValues)
+    return report_error(FDW_ERR_INVALID_ARG,
+                        "fdw_misfit_noalloc: n = %lld exceeds the maximum of %lld values "
+                        "(static scratch of %lld chunk sums); use fdw_misfit",
+                        n, kNoAllocMaxValues, kNoAllocChunks);
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return report_error(FDW_ERR_CUDA, "fdw_misfit_noalloc: no usable current device");
+  }
+  double *scratch;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      // set-up, once per device, with that device current
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_misfit_scratch);
+      if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return report_error(FDW_ERR_CUDA, "fdw_misfit_noalloc: cudaGetSymbolAddress: %s",
+                            cudaGetErrorString(e));
+      }
+      g_scratch_addr[dev] = (double *)p;
+    }
+    scratch = g_scratch_addr[dev];
+  }
+  e = launch_misfit(d, d_obs, n, residual, J, scratch, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return report_error(FDW_ERR_CUDA, "fdw_misfit_noalloc: %s", cudaGetErrorString(e));
+  }
+  return FDW_OK;
+}
 
 extern "C" int fdw_misfit(const double *d, const double *d_obs, long long n, double *residual,
                           double *J, void *stream) {

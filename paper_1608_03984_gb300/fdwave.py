@@ -64,6 +64,7 @@ _SIGS = {
     "fdw_get_source_adjoint": ([_P, _P, _I], _I),
     "fdw_get_adjoint_wavefield": ([_P, _I, _P, _I], _I),
     "fdw_misfit": ([_P, _P, ctypes.c_longlong, _P, _P, _P], _I),
+    "fdw_misfit_noalloc": ([_P, _P, ctypes.c_longlong, _P, _P, _P], _I),
     "fdw_profile_begin": ([_P, _I], _I),
     "fdw_profile_end": ([_P, ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
 }
