@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--zchunks", type=int, default=0, help="CTAs along z (0 default)")
     p.add_argument("--no-tti", action="store_true")
     p.add_argument("--no-fwi", action="store_true")
+    p.add_argument("--no-storage", action="store_true")
     p.add_argument("--fwi-n", type=int, default=256)
     p.add_argument("--fwi-nt", type=int, default=2000)
     p.add_argument("--fwi-shots-side", type=int, default=4)
@@ -347,6 +348,11 @@ def run_fdwave(args, orders):
     tti = None
     if not args.no_tti:
         tti = run_tti(args, stream, steps=min(args.steps, 30), warmup=3)
+    storage = None
+    if not args.no_storage:
+        storage = run_storage(args, base, stream,
+                              {o: per_order[str(o)]["kernel_ms"] for o in orders},
+                              steps=min(args.steps, 30), warmup=3)
     fwi_res = None
     if not args.no_fwi and world == 1:
         fwi_res = run_fwi(args)
@@ -368,7 +374,7 @@ def run_fdwave(args, orders):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_dict(args, orders, base),
             "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu, "tti": tti,
-            "fwi": fwi_res,
+            "fwi": fwi_res, "storage": storage,
             "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
         }
         print(json.dumps(line), flush=True)
@@ -411,6 +417,74 @@ def run_tti(args, stream, steps, warmup):
             out.setdefault(str(order), {})[st] = {
                 "kernel_ms": avg, "gpts": gpts, "achieved_gbs": gpts * bpp,
                 "frac_of_measured_hbm": gpts * bpp / hbm}
+    return out
+
+
+def storage_errors():
+    """Relative L2 errors against the FP64 oracle of FP32 / BF16 / FP16
+    storage on reduced problems (acoustic 48^3 + 10 sponge, order 8, 150
+    steps; TTI 36^3 + 8 sponge, order 8, 100 steps), per field."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_1608_03984_gb300 import fdwave, synth
+
+    def rel(a, b):
+        return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+    out = {"acoustic": {}, "tti": {}}
+    w = synth.two_layer(n=48, nb=10, order=8, nt=150, nrec=16)
+    ref = O.acoustic_forward(O.Setup(w.vp, w.h, w.nb, w.order, w.dt), w.src_xyz, w.wavelet,
+                             w.nt, w.rec_xyz)
+    for st in ("f32", "bf16", "f16"):
+        s = fdwave.Solver(w.n, w.h, w.nb, w.order, storage=st)
+        s.set_model(w.vp).set_dt(w.dt).set_sources(w.src_xyz, w.wavelet)
+        s.set_receivers(w.rec_xyz, w.nt).step(w.nt)
+        out["acoustic"][st] = {"traces": rel(s.traces(), ref["traces"]),
+                               "u": rel(s.wavefield(0, 0), ref["u"])}
+        s.close()
+    t = synth.random_tti(n=36, nb=8, order=8, nt=100, nrec_side=6)
+    ref = O.tti_forward(O.Setup(t.vp, t.h, t.nb, t.order, t.dt, eps=t.eps, delta=t.delta,
+                                theta=t.theta, phi=t.phi), t.src_xyz, t.wavelet, t.nt, t.rec_xyz)
+    for st in ("f32", "bf16", "f16"):
+        s = fdwave.Solver(t.n, t.h, t.nb, t.order, equation="tti", storage=st)
+        s.set_model(t.vp, t.eps, t.delta, t.theta, t.phi).set_dt(t.dt)
+        s.set_sources(t.src_xyz, t.wavelet).set_receivers(t.rec_xyz, t.nt).step(t.nt)
+        out["tti"][st] = {"traces": rel(s.traces(), ref["traces"]), "p": rel(s.wavefield(0, 0), ref["p"]),
+                          "r": rel(s.wavefield(1, 0), ref["r"])}
+        s.close()
+    out["problems"] = ("acoustic two-layer 48^3 + 10 sponge, order 8, 150 steps; "
+                       "TTI random 36^3 + 8 sponge, order 8, 100 steps; relative L2 vs FP64 oracle")
+    return out
+
+
+def run_storage(args, base, stream, fp32_kernel_ms, steps, warmup):
+    """16-bit storage (BF16 / FP16, FP32 arithmetic) of the acoustic step on
+    the 592^3 workload at every order of the sweep: kernel time and speedup
+    over FP32 (8 B per point instead of 16)."""
+    import torch
+    from paper_1608_03984_gb300 import fdwave
+    hbm, _ = peaks()
+    out = {}
+    for o in sorted(fp32_kernel_ms):
+        if o not in fp32_kernel_ms:
+            continue
+        for st in ("bf16", "f16"):
+            s = fdwave.Solver(base.n, base.h, base.nb, o, storage=st, stream=stream)
+            s.set_model(base.vp).set_dt(base.dt).set_sources(base.src_xyz, base.wavelet)
+            s.set_receivers(base.rec_xyz, steps + warmup + 2)
+            s.step(warmup)
+            torch.cuda.synchronize()
+            s.profile_begin(steps)
+            s.step(steps)
+            ms, n = s.profile_end()
+            s.check()
+            s.close()
+            avg = ms / max(n, 1)
+            gpts = base.points / (avg / 1e3) / 1e9
+            out.setdefault(str(o), {})[st] = {
+                "kernel_ms": avg, "gpts": gpts, "speedup_vs_f32": fp32_kernel_ms[o] / avg,
+                "achieved_gbs": gpts * 8, "frac_of_measured_hbm": gpts * 8 / hbm}
+    out["errors_vs_fp64_oracle"] = storage_errors()
     return out
 
 

@@ -114,6 +114,21 @@ double fdw_max_stable_dt(const fdw_solver *s);
 int fdw_set_sponge(fdw_solver *s, double vref, double R);
 
 /*
+ * Storage scale S: the buffers hold S times the physical wavefield (the
+ * equations are linear, so this only moves the values within the storage
+ * type's range). Sources are injected times S; traces, fdw_get_wavefield,
+ * fdw_set_wavefield, the adjoint and the gradient undo it, so every value
+ * a caller sees is physical. scale = 0 (default) chooses at fdw_set_dt:
+ * for FP16 storage the power of two that makes the stored increment of a
+ * unit source about 256 (the far field then stays in FP16's normal range),
+ * otherwise 1. Set it before stepping (stored levels are not rescaled);
+ * dt is marked unset. fdw_get_field_scale returns the scale in use.
+ * Errors: INVALID_ARG (scale < 0 or non-finite).
+ */
+int fdw_set_field_scale(fdw_solver *s, double scale);
+double fdw_get_field_scale(const fdw_solver *s);
+
+/*
  * Set dt (seconds): computes c = dt^2 v^2 and the sponge damping.
  * Errors: UNSTABLE_DT if dt > fdw_max_stable_dt, STATE before set_model.
  */

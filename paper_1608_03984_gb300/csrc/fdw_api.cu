@@ -72,6 +72,9 @@ struct fdw_solver {
   bool model_set = false, dt_set = false;
   double vmax = 0, vmax_eff = 0, dt = 0;
   double sponge_vref = 0.0, sponge_R = 1e-3;  // vref <= 0: the model's vmax
+  // stored wavefields are fscale x the physical ones (keeps FP16 storage in
+  // its normal range); fscale_req = 0 means automatic
+  double fscale = 1.0, fscale_req = 0.0;
 
   int nsrc = 0, nt_src = 0;
   int *src_corner = nullptr;
@@ -337,6 +340,8 @@ int enqueue_sparse(fdw_solver *s, int cur, cudaStream_t st) {
   S.src_corner = s->src_corner;
   S.src_w = s->src_w;
   S.wavelet = s->wavelet;
+  S.amp_scale = (float)s->fscale;
+  S.trace_scale = 1.0 / s->fscale;
   S.nt_src = s->nt_src;
   S.nrec = s->nrec;
   S.rec_corner = s->rec_corner;
@@ -592,6 +597,16 @@ extern "C" int fdw_set_dt(fdw_solver *s, double dt) {
   } else {
     CK(launch_coef_tti(s->storage, s->vp, s->eps, s->delta, s->theta, s->phi, s->nx, s->ny, s->nz,
                        s->nb, s->d, doh, s->c, s->e, s->dl, s->ax, s->ay, s->stream));
+  }
+  // field scale: FP16 storage keeps the injected increment of a unit source
+  // near 256 (a power of two, so scaling is exact); other storage types 1
+  if (s->fscale_req > 0.0) {
+    s->fscale = s->fscale_req;
+  } else if (s->storage == FDW_F16) {
+    const double cmax = (s->vmax_eff * dt / s->h) * (s->vmax_eff * dt / s->h);
+    s->fscale = exp2(round(log2(256.0 * s->h / (cmax > 0.0 ? cmax : 1.0))));
+  } else {
+    s->fscale = 1.0;
   }
   s->dt_set = true;
   drop_graphs(s);
@@ -907,9 +922,11 @@ extern "C" int fdw_adjoint_step(fdw_solver *s, int nsteps) {
     S.residual = s->residual;
     S.nt_res = s->nt_res;
     S.res_scale = (float)(s->h * s->h);
+    S.amp_scale = (float)s->fscale;
+    S.trace_scale = 1.0 / s->fscale;
     S.adjoint = 1;
     S.src_adj = s->src_adj;
-    S.src_adj_scale = (float)(1.0 / (s->h * s->h));
+    S.src_adj_scale = (float)(1.0 / (s->h * s->h * s->fscale));
     CK(launch_sparse(S, s->stream));
     if (s->adj_grad && j >= 1) {
       // term n = j - 1: mu_j (P u_j - 2 u_{j-1} + Q u_{j-2}), u_{-1} = 0
@@ -939,7 +956,8 @@ extern "C" int fdw_get_gradient(fdw_solver *s, double *grad_m, int ptr_is_device
   double *dst = grad_m;
   if (!ptr_is_device) CK(dmalloc(&dst, n * sizeof(double)));
   cudaError_t e = launch_grad_physical(s->grad64, s->d, s->nx, s->ny, s->nz, s->nb,
-                                       -1.0 / (s->dt * s->dt), dst, s->stream);
+                                       -1.0 / (s->dt * s->dt * s->fscale * s->fscale), dst,
+                                       s->stream);
   if (e == cudaSuccess && !ptr_is_device) {
     e = cudaMemcpyAsync(grad_m, dst, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -968,7 +986,8 @@ extern "C" int fdw_get_adjoint_wavefield(const fdw_solver *cs, int level, float 
   const size_t n = (size_t)s->d.NX * s->d.NY * s->d.NZ;
   float *dst = out;
   if (!ptr_is_device) CK(dmalloc(&dst, n * sizeof(float)));
-  cudaError_t e = launch_unpack(s->storage, s->a[level == 0 ? s->acur : 1 - s->acur], s->d, dst, s->stream);
+  cudaError_t e = launch_unpack(s->storage, s->a[level == 0 ? s->acur : 1 - s->acur], s->d, dst,
+                                (float)(1.0 / s->fscale), s->stream);
   if (e == cudaSuccess && !ptr_is_device) {
     e = cudaMemcpyAsync(out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -1052,7 +1071,8 @@ extern "C" int fdw_get_wavefield(const fdw_solver *cs, int field, int level, flo
   const size_t n = (size_t)s->d.NX * s->d.NY * s->d.NZ;
   float *dst = out;
   if (!ptr_is_device) CK(dmalloc(&dst, n * sizeof(float)));
-  cudaError_t e = launch_unpack(s->storage, level_ptr(s, field, level), s->d, dst, s->stream);
+  cudaError_t e = launch_unpack(s->storage, level_ptr(s, field, level), s->d, dst,
+                                (float)(1.0 / s->fscale), s->stream);
   if (e == cudaSuccess && !ptr_is_device) {
     e = cudaMemcpyAsync(out, dst, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -1079,7 +1099,8 @@ extern "C" int fdw_set_wavefield(fdw_solver *s, int field, int level, const floa
     }
     src = tmp;
   }
-  cudaError_t e = launch_pack(s->storage, src, level_ptr(s, field, level), s->d, s->stream);
+  cudaError_t e = launch_pack(s->storage, src, level_ptr(s, field, level), s->d, (float)s->fscale,
+                              s->stream);
   if (tmp) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     cudaFree(tmp);
@@ -1105,6 +1126,17 @@ extern "C" int fdw_check(fdw_solver *s, int check_finite) {
   }
   return FDW_OK;
 }
+
+extern "C" int fdw_set_field_scale(fdw_solver *s, double scale) {
+  if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
+  if (!(scale >= 0.0) || !isfinite(scale)) return fail(FDW_ERR_INVALID_ARG, "scale must be >= 0");
+  s->fscale_req = scale;
+  s->dt_set = false;
+  drop_graphs(s);
+  return FDW_OK;
+}
+
+extern "C" double fdw_get_field_scale(const fdw_solver *s) { return s ? s->fscale : -1.0; }
 
 extern "C" int fdw_set_sponge(fdw_solver *s, double vref, double R) {
   if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");

@@ -158,7 +158,9 @@ struct SparseLaunch {
   float res_scale;           // h^2: c' = c / h^2 is stored, the adjoint source is c R^T res
   int adjoint;
   double *src_adj;           // [nt_src][nsrc] adjoint w.r.t. the wavelet, or null
-  float src_adj_scale;       // 1 / h^2
+  float src_adj_scale;       // 1 / (h^2 S)
+  float amp_scale;           // S: stored fields are S x the physical ones
+  double trace_scale;        // 1 / S
 };
 cudaError_t launch_sparse(const SparseLaunch &L, cudaStream_t st);
 
@@ -181,9 +183,11 @@ cudaError_t launch_coef_tti(int storage, const float *vp, const float *eps, cons
                             void *ax, void *ay, cudaStream_t st);
 cudaError_t launch_max_velocity(const float *vp, const float *eps, long n, float *out3,
                                 cudaStream_t st);
-cudaError_t launch_pack(int storage, const float *src, void *dst, Dims d,
-                        cudaStream_t st);   // dense [NZ][NY][NX] f32 -> padded storage
-cudaError_t launch_unpack(int storage, const void *src, Dims d, float *dst, cudaStream_t st);
+// dense [NZ][NY][NX] f32 <-> padded storage, values multiplied by `scale`
+cudaError_t launch_pack(int storage, const float *src, void *dst, Dims d, float scale,
+                        cudaStream_t st);
+cudaError_t launch_unpack(int storage, const void *src, Dims d, float *dst, float scale,
+                          cudaStream_t st);
 cudaError_t launch_nonfinite(int storage, const void *f, Dims d, int *flag, cudaStream_t st);
 
 }  // namespace fdw

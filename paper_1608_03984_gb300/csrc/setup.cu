@@ -90,24 +90,24 @@ __global__ void max_velocity_kernel(const float *__restrict__ vp, const float *_
 }
 
 template <typename T>
-__global__ void pack_kernel(const float *__restrict__ src, T *__restrict__ dst, Dims d) {
+__global__ void pack_kernel(const float *__restrict__ src, T *__restrict__ dst, Dims d, float scale) {
   const size_t n = d.vol();
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
        p += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(p % d.Xp);
     const size_t row = p / d.Xp;
-    dst[p] = St<T>::st(i < d.NX ? src[row * d.NX + i] : 0.f);
+    dst[p] = St<T>::st(i < d.NX ? scale * src[row * d.NX + i] : 0.f);
   }
 }
 
 template <typename T>
-__global__ void unpack_kernel(const T *__restrict__ src, float *__restrict__ dst, Dims d) {
+__global__ void unpack_kernel(const T *__restrict__ src, float *__restrict__ dst, Dims d, float scale) {
   const size_t n = (size_t)d.NX * d.NY * d.NZ;
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
        p += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(p % d.NX);
     const size_t row = p / d.NX;
-    dst[p] = St<T>::ld(src[row * d.Xp + i]);
+    dst[p] = scale * St<T>::ld(src[row * d.Xp + i]);
   }
 }
 
@@ -159,14 +159,16 @@ cudaError_t launch_max_velocity(const float *vp, const float *eps, long n, float
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack(int storage, const float *src, void *dst, Dims d, cudaStream_t st) {
-  FDW_DISPATCH(storage, (pack_kernel<T><<<grid_for(d.vol()), 256, 0, st>>>(src, (T *)dst, d)));
+cudaError_t launch_pack(int storage, const float *src, void *dst, Dims d, float scale,
+                        cudaStream_t st) {
+  FDW_DISPATCH(storage, (pack_kernel<T><<<grid_for(d.vol()), 256, 0, st>>>(src, (T *)dst, d, scale)));
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack(int storage, const void *src, Dims d, float *dst, cudaStream_t st) {
+cudaError_t launch_unpack(int storage, const void *src, Dims d, float *dst, float scale,
+                          cudaStream_t st) {
   FDW_DISPATCH(storage, (unpack_kernel<T><<<grid_for((size_t)d.NX * d.NY * d.NZ), 256, 0, st>>>(
-                            (const T *)src, dst, d)));
+                            (const T *)src, dst, d, scale)));
   return cudaGetLastError();
 }
 

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) inject_kernel(SparseLaunch L) {
       const float amp = L.wavelet[(size_t)n * L.nsrc + s];
       const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[k];
       const float cc = St<T>::ld(((const T *)L.c)[p]);
-      const float v = cc * wt * amp * __frcp_rn(1.f + gh);
+      const float v = cc * wt * (amp * L.amp_scale) * __frcp_rn(1.f + gh);
       atomic_add_st<T>((T *)L.f0 + p, v);
       if (L.f1) atomic_add_st<T>((T *)L.f1 + p, v);
     }
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(256) gather_kernel(SparseLaunch L) {
     const float v = St<T>::ld(f[(size_t)k * plane + (size_t)j * L.d.Xp + i]);
     acc += (double)wt * (double)v;
   }
-  L.traces[(size_t)n1 * L.nrec + r] = acc;
+  L.traces[(size_t)n1 * L.nrec + r] = acc * L.trace_scale;
 }
 
 // Adjoint step producing level k = *step - 1 (the counter is decremented by
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) adjoint_spread_kernel(SparseLaunch L) {
   const float res = (float)L.residual[(size_t)k * L.nrec + s];
   const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[kk];
   const float cc = St<T>::ld(((const T *)L.c)[p]);
-  atomic_add_st<T>((T *)L.f0 + p, cc * L.res_scale * wt * res * __frcp_rn(1.f + gh));
+  atomic_add_st<T>((T *)L.f0 + p, cc * L.res_scale * wt * (res * L.amp_scale) * __frcp_rn(1.f + gh));
 }
 
 template <typename T>

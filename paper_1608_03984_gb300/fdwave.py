@@ -55,6 +55,8 @@ _SIGS = {
     "fdw_set_tile_config": ([_P, _I], _I),
     "fdw_get_tile_config": ([_P], _I),
     "fdw_set_sponge": ([_P, _D, _D], _I),
+    "fdw_set_field_scale": ([_P, _D], _I),
+    "fdw_get_field_scale": ([_P], _D),
     "fdw_history_begin": ([_P, _I], _I),
     "fdw_history_end": ([_P], _I),
     "fdw_adjoint_begin": ([_P, _P, _I, _I, _I], _I),
@@ -224,6 +226,15 @@ class Solver:
         """Fix the sponge's velocity scale (vref <= 0: the model's vmax)."""
         _chk(lib().fdw_set_sponge(self._h, float(vref), float(R)))
         return self
+
+    def set_field_scale(self, scale=0.0):
+        """Storage scale of the wavefields (0: automatic, see fdwave.h)."""
+        _chk(lib().fdw_set_field_scale(self._h, float(scale)))
+        return self
+
+    @property
+    def field_scale(self):
+        return lib().fdw_get_field_scale(self._h)
 
     def max_stable_dt(self):
         return lib().fdw_max_stable_dt(self._h)
