@@ -367,6 +367,14 @@ def run_fdwave(args, orders):
                "sample": "16 x %d x %d slab of the %dx%dx%d grid per order (orders %s), FP64 oracle, "
                          "%.1f s" % (ny, nx, nz, ny, nx, "/".join(map(str, orders)), sec)}
 
+    # the paper's model restated for this GPU (measured HBM bandwidth; FP32
+    # peak from 152 SMs x 128 FMA lanes x 2 FLOP x the measured SM clock)
+    sm_ghz = (clk.get("sm_mhz") or 2070.0) / 1e3
+    paper = opmodel.restate(hbm, opmodel.fp32_peak_gflops(clock_ghz=sm_ghz))
+    for o, v in paper["table_cost"].items():
+        if o in per_order:  # measured time for the Table tab:stab problem at this order
+            v["measured_runtime_s"] = v["N"] * v["nt"] / (per_order[o]["kernel_gpts"] * 1e9)
+
     if rank == 0:
         line = {
             "metric": "Gpts/s per timestep", "value": value, "unit": "Gpts/s", "n_gpus": world,
@@ -374,7 +382,7 @@ def run_fdwave(args, orders):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_dict(args, orders, base),
             "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu, "tti": tti,
-            "fwi": fwi_res, "storage": storage,
+            "fwi": fwi_res, "storage": storage, "paper_model_gb300": paper,
             "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
         }
         print(json.dumps(line), flush=True)

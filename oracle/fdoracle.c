@@ -637,3 +637,136 @@ int or_acoustic_adjoint(int nx, int ny, int nz, int order, double h, int nb, dou
     free(m2); free(m1);
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Learned closure: a small 3x3x3 convolutional network                      */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * The paper has no learned component (its cost-benefit section trades grid
+ * spacing against stencil order); the closure corrects a coarse low-order
+ * step toward the fine high-order one. Network: conv 3 -> H, ReLU,
+ * conv H -> H, ReLU, conv H -> 1, all 3x3x3 "valid" convolutions (each
+ * shrinks the box by one point per face):
+ *   out[co][z][y][x] = b[co] + sum_ci sum_{a,b,c in 0..2}
+ *                      W[co][ci][(a*3+b)*3+c] in[ci][z+a][y+b][x+c].
+ * Parameters, concatenated: W1[H][3][27], b1[H], W2[H][H][27], b2[H],
+ * W3[1][H][27], b3[1].
+ */
+static void conv_valid(int ci, int co, int nz, int ny, int nx, const double *in, const double *w,
+                       const double *b, int relu, double *out)
+{
+    const int oz = nz - 2, oy = ny - 2, ox = nx - 2;
+    for (int o = 0; o < co; ++o)
+        for (int z = 0; z < oz; ++z)
+            for (int y = 0; y < oy; ++y)
+                for (int x = 0; x < ox; ++x) {
+                    double s = b[o];
+                    for (int i = 0; i < ci; ++i)
+                        for (int a = 0; a < 3; ++a)
+                            for (int bb = 0; bb < 3; ++bb)
+                                for (int c = 0; c < 3; ++c)
+                                    s += w[((long)o * ci + i) * 27 + (a * 3 + bb) * 3 + c] *
+                                         in[(((long)i * nz + z + a) * ny + y + bb) * nx + x + c];
+                    out[(((long)o * oz + z) * oy + y) * ox + x] = (relu && s < 0.0) ? 0.0 : s;
+                }
+}
+
+/* d(loss)/d(in) and d(loss)/d(w, b) of conv_valid, given g = d(loss)/d(out)
+ * (after the ReLU mask of the layer's own output has been applied). */
+static void conv_valid_backward(int ci, int co, int nz, int ny, int nx, const double *in,
+                                const double *w, const double *g, double *gin, double *gw,
+                                double *gb)
+{
+    const int oz = nz - 2, oy = ny - 2, ox = nx - 2;
+    if (gin) memset(gin, 0, sizeof(double) * (size_t)ci * nz * ny * nx);
+    for (int o = 0; o < co; ++o)
+        for (int z = 0; z < oz; ++z)
+            for (int y = 0; y < oy; ++y)
+                for (int x = 0; x < ox; ++x) {
+                    const double gv = g[(((long)o * oz + z) * oy + y) * ox + x];
+                    gb[o] += gv;
+                    for (int i = 0; i < ci; ++i)
+                        for (int a = 0; a < 3; ++a)
+                            for (int bb = 0; bb < 3; ++bb)
+                                for (int c = 0; c < 3; ++c) {
+                                    const long t = ((long)o * ci + i) * 27 + (a * 3 + bb) * 3 + c;
+                                    const long p = (((long)i * nz + z + a) * ny + y + bb) * nx + x + c;
+                                    gw[t] += gv * in[p];
+                                    if (gin) gin[p] += gv * w[t];
+                                }
+                }
+}
+
+long or_closure_num_params(int H)
+{
+    return (long)H * 3 * 27 + H + (long)H * H * 27 + H + (long)H * 27 + 1;
+}
+
+/*
+ * Forward pass of one sample: in [3][nz][ny][nx] -> out [nz-6][ny-6][nx-6].
+ * a1 [H][nz-2]..., a2 [H][nz-4]... receive the (post-ReLU) activations
+ * when non-NULL.
+ */
+int or_closure_forward(int H, int nz, int ny, int nx, const double *params, const double *in,
+                       double *a1, double *a2, double *out)
+{
+    if (H < 1 || nz < 7 || ny < 7 || nx < 7) return -1;
+    const double *W1 = params, *b1 = W1 + (long)H * 3 * 27, *W2 = b1 + H, *b2 = W2 + (long)H * H * 27,
+                 *W3 = b2 + H, *b3 = W3 + (long)H * 27;
+    const long n1 = (long)H * (nz - 2) * (ny - 2) * (nx - 2), n2 = (long)H * (nz - 4) * (ny - 4) * (nx - 4);
+    double *t1 = a1 ? a1 : malloc(sizeof(double) * n1);
+    double *t2 = a2 ? a2 : malloc(sizeof(double) * n2);
+    if (!t1 || !t2) return -2;
+    conv_valid(3, H, nz, ny, nx, in, W1, b1, 1, t1);
+    conv_valid(H, H, nz - 2, ny - 2, nx - 2, t1, W2, b2, 1, t2);
+    conv_valid(H, 1, nz - 4, ny - 4, nx - 4, t2, W3, b3, 0, out);
+    if (!a1) free(t1);
+    if (!a2) free(t2);
+    return 0;
+}
+
+/*
+ * Mean-squared error of a batch and its gradient w.r.t. the parameters:
+ * loss = (1/M) sum over samples and output points of (out - target)^2,
+ * M = batch * (nz-6)(ny-6)(nx-6). in [batch][3][nz][ny][nx], target
+ * [batch][nz-6][ny-6][nx-6]; grad (may be NULL) receives d loss / d params.
+ */
+int or_closure_loss_grad(int H, int batch, int nz, int ny, int nx, const double *params,
+                         const double *in, const double *target, double *loss, double *grad)
+{
+    if (batch < 1) return -1;
+    const long np_ = or_closure_num_params(H);
+    const double *W2 = params + (long)H * 3 * 27 + H, *W3 = W2 + (long)H * H * 27 + H;
+    double *gW1 = grad, *gb1 = grad ? gW1 + (long)H * 3 * 27 : NULL, *gW2 = grad ? gb1 + H : NULL,
+           *gb2 = grad ? gW2 + (long)H * H * 27 : NULL, *gW3 = grad ? gb2 + H : NULL,
+           *gb3 = grad ? gW3 + (long)H * 27 : NULL;
+    if (grad) memset(grad, 0, sizeof(double) * np_);
+    const long s0 = (long)nz * ny * nx, s1 = (long)(nz - 2) * (ny - 2) * (nx - 2),
+               s2 = (long)(nz - 4) * (ny - 4) * (nx - 4), s3 = (long)(nz - 6) * (ny - 6) * (nx - 6);
+    double *a1 = malloc(sizeof(double) * H * s1), *a2 = malloc(sizeof(double) * H * s2);
+    double *out = malloc(sizeof(double) * s3), *g3 = malloc(sizeof(double) * s3);
+    double *g2 = malloc(sizeof(double) * H * s2), *g1 = malloc(sizeof(double) * H * s1);
+    if (!a1 || !a2 || !out || !g3 || !g2 || !g1) return -2;
+    const double M = (double)batch * s3;
+    double L = 0.0;
+    for (int b = 0; b < batch; ++b) {
+        or_closure_forward(H, nz, ny, nx, params, in + b * 3 * s0, a1, a2, out);
+        for (long p = 0; p < s3; ++p) {
+            const double r = out[p] - target[b * s3 + p];
+            L += r * r / M;
+            g3[p] = 2.0 * r / M;
+        }
+        if (!grad) continue;
+        conv_valid_backward(H, 1, nz - 4, ny - 4, nx - 4, a2, W3, g3, g2, gW3, gb3);
+        for (long p = 0; p < H * s2; ++p)
+            if (a2[p] <= 0.0) g2[p] = 0.0;  /* ReLU of layer 2 */
+        conv_valid_backward(H, H, nz - 2, ny - 2, nx - 2, a1, W2, g2, g1, gW2, gb2);
+        for (long p = 0; p < H * s1; ++p)
+            if (a1[p] <= 0.0) g1[p] = 0.0;  /* ReLU of layer 1 */
+        conv_valid_backward(3, H, nz, ny, nx, in + b * 3 * s0, params, g1, NULL, gW1, gb1);
+    }
+    if (loss) *loss = L;
+    free(a1); free(a2); free(out); free(g3); free(g2); free(g1);
+    return 0;
+}

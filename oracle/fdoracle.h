@@ -55,6 +55,12 @@ int or_acoustic_adjoint(int nx, int ny, int nz, int order, double h, int nb, dou
                         int nsrc, const double *src_xyz, double *wavelet_adj,
                         const double *history, double *grad_m);
 
+long or_closure_num_params(int H);
+int or_closure_forward(int H, int nz, int ny, int nx, const double *params, const double *in,
+                       double *a1, double *a2, double *out);
+int or_closure_loss_grad(int H, int batch, int nz, int ny, int nx, const double *params,
+                         const double *in, const double *target, double *loss, double *grad);
+
 #ifdef __cplusplus
 }
 #endif

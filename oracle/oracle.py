@@ -342,3 +342,42 @@ def extend_adjoint(g, nb):
         inner[-1] += a[a.shape[0] - nb:].sum(axis=0)
         g = np.moveaxis(inner, 0, ax)
     return np.ascontiguousarray(g)
+
+
+# --------------------------------------------------------------------------
+# learned closure (3x3x3 conv net, fdoracle.c)
+# --------------------------------------------------------------------------
+
+def closure_num_params(hidden=16):
+    L = lib()
+    L.or_closure_num_params.argtypes = [_I]
+    L.or_closure_num_params.restype = ctypes.c_long
+    return int(L.or_closure_num_params(hidden))
+
+
+def closure_forward(params, x, hidden=16):
+    """x [3, nz, ny, nx] -> out [nz-6, ny-6, nx-6] (valid 3x3x3 convolutions)."""
+    L = lib()
+    L.or_closure_forward.argtypes = [_I, _I, _I, _I, _D, _D, _D, _D, _D]
+    L.or_closure_forward.restype = _I
+    params, x = _f64(params), _f64(x)
+    _, nz, ny, nx = x.shape
+    out = np.zeros((nz - 6, ny - 6, nx - 6))
+    _chk(L.or_closure_forward(hidden, nz, ny, nx, _p(params), _p(x), None, None, _p(out)),
+         "closure_forward")
+    return out
+
+
+def closure_loss_grad(params, x, target, hidden=16, grad=True):
+    """Mean-squared error of a batch x [B, 3, nz, ny, nx] against target
+    [B, nz-6, ny-6, nx-6] and its gradient w.r.t. the parameters."""
+    L = lib()
+    L.or_closure_loss_grad.argtypes = [_I, _I, _I, _I, _I, _D, _D, _D, _D, _D]
+    L.or_closure_loss_grad.restype = _I
+    params, x, target = _f64(params), _f64(x), _f64(target)
+    B, _, nz, ny, nx = x.shape
+    loss = np.zeros(1)
+    g = np.zeros(params.size) if grad else None
+    _chk(L.or_closure_loss_grad(hidden, B, nz, ny, nx, _p(params), _p(x), _p(target), _p(loss),
+                                _p(g)), "closure_loss_grad")
+    return float(loss[0]), g

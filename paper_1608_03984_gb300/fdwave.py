@@ -189,8 +189,10 @@ class Solver:
         self.comp_shape = (nz + 2 * nb, ny + 2 * nb, nx + 2 * nb)
         self.stream = _stream_handle(stream)
         handle = _P()
+        # VTI (Eq. vVTI) is the TTI system with a vertical symmetry axis
+        eq = EQUATION["tti" if equation == "vti" else equation]
         _chk(lib().fdw_create(ctypes.byref(handle), nx, ny, nz, self.h, self.nb,
-                              EQUATION[equation], self.order, STORAGE[storage], self.stream))
+                              eq, self.order, STORAGE[storage], self.stream))
         self._h = handle
         self.nrec = 0
         self.nt_rec = 0
@@ -215,6 +217,15 @@ class Solver:
 
     # -- set-up -----------------------------------------------------------
     def set_model(self, vp, eps=None, delta=None, theta=None, phi=None):
+        if self.equation == "vti":
+            if theta is not None or phi is not None:
+                raise ValueError("VTI has a vertical axis: no theta/phi")
+            if _is_torch(vp):
+                import torch
+                theta = torch.zeros_like(vp, dtype=torch.float32)
+            else:
+                theta = np.zeros(np.shape(vp), dtype=np.float32)
+            phi = theta
         ptrs = [_ptr(a, np.float32) for a in (vp, eps, delta, theta, phi)]
         dev = ptrs[0][1]
         if any(p[0] is not None and p[1] != dev for p in ptrs):

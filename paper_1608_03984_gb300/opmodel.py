@@ -90,6 +90,35 @@ def cfl_limit(order: int, a1: float = 4.0) -> float:
     return math.sqrt(a1 / a2(order))
 
 
+def fp32_peak_gflops(sms: int = 152, fma_lanes_per_sm: int = 128, clock_ghz: float = 2.07) -> float:
+    """FP32 peak from unit counts: every SM issues fma_lanes_per_sm FMAs
+    (2 FLOPs each) per clock."""
+    return sms * fma_lanes_per_sm * 2 * clock_ghz
+
+
+def restate(b_gbs: float, f_gflops: float, orders=(2, 4, 6, 8, 12, 16, 18, 24)):
+    """The paper's model on a machine of bandwidth b_gbs and peak f_gflops:
+    the ridge I_min = F/B, the minimum compute-bound order per equation
+    (Section "Stencil operators"), and the Table tab:cost estimate for the
+    Table tab:stab set-ups: GFLOPS = min(I B, F) and the runtime."""
+    i_min = f_gflops / b_gbs
+    out = {"B_GBs": b_gbs, "F_GFLOPs": f_gflops, "I_min": i_min,
+           "min_compute_bound_order": {eq: min_compute_bound_order(eq, i_min)
+                                       for eq in ("acoustic", "vti", "tti")},
+           "table_cost": {}}
+    ps = {2: 6, 6: 5, 12: 4, 18: 3, 24: 2}  # Table tab:stab
+    for order, p in ps.items():
+        k = order + 1
+        st = cost_setup(order, p)
+        nt = math.ceil(st["nt_exact"])
+        gflop = flops_per_point("acoustic", k) * st["N"] * nt / 1e9
+        gflops = roofline(oi("acoustic", k), b_gbs, f_gflops)
+        out["table_cost"][str(order)] = {"I_alg": oi("acoustic", k), "GFLOPs": gflop,
+                                         "GFLOPS": gflops, "runtime_s": gflop / gflops,
+                                         "N": st["N"], "nt": nt}
+    return out
+
+
 def cost_setup(order: int, p: float, n2: int = 500, nt2: int = 1000):
     """Table tab:stab row for a physical box of n2 points at 2nd order
     (h = 6/p in units of the 2nd-order spacing, unit velocity)."""

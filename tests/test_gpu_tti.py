@@ -108,3 +108,20 @@ def test_isotropic_tti_equals_acoustic(fdw):
     assert rel(s.wavefield(1, 0), ua) <= 1e-5
     s.close()
     a.close()
+
+
+def test_vti_matches_oracle(fdw, O):
+    """VTI (Eq. vVTI, D_xx read as the horizontal Laplacian) through the
+    binding's "vti" equation: the TTI step with a vertical axis."""
+    w = small_tti(order=8, nt=30, seed=81)
+    s = fdw.Solver(w.n, w.h, w.nb, w.order, equation="vti")
+    s.set_model(w.vp, w.eps, w.delta).set_dt(w.dt)
+    s.set_sources(w.src_xyz, w.wavelet).set_receivers(w.rec_xyz, w.nt)
+    s.step(w.nt)
+    z = np.zeros_like(w.theta)
+    ref = O.tti_forward(O.Setup(w.vp, w.h, w.nb, w.order, w.dt, eps=w.eps, delta=w.delta,
+                                theta=z, phi=z), w.src_xyz, w.wavelet, w.nt, w.rec_xyz)
+    assert rel(s.traces(), ref["traces"]) <= RUN_TOL
+    assert rel(s.wavefield(0, 0), ref["p"]) <= RUN_TOL
+    assert rel(s.wavefield(1, 0), ref["r"]) <= RUN_TOL
+    s.close()

@@ -123,3 +123,15 @@ def test_cfl_limits():
     assert lim[4] == pytest.approx(0.5)
     assert all(v > 0.4 for v in lim.values())
     assert all(lim[a] > lim[b] for a, b in [(2, 4), (4, 8), (8, 12), (12, 16)])
+
+
+def test_gb300_restatement_structure():
+    """The restated model reproduces the paper's Xeon numbers when given the
+    Xeon's achievable peaks (I_min 9.3 -> orders 24 / 26 / 6)."""
+    r = opmodel.restate(100.0, 930.0)
+    assert r["I_min"] == pytest.approx(9.3)
+    assert r["min_compute_bound_order"] == {"acoustic": 24, "vti": 26, "tti": 6}
+    assert r["table_cost"]["2"]["GFLOPS"] == pytest.approx(137.5)
+    assert r["table_cost"]["2"]["runtime_s"] == pytest.approx(20.0, rel=1e-9)
+    g = opmodel.restate(6784.2, opmodel.fp32_peak_gflops())
+    assert g["min_compute_bound_order"]["tti"] == 8
