@@ -318,6 +318,70 @@ int fdw_misfit_noalloc(const double *d, const double *d_obs, long long n, double
 int fdw_get_adjoint_wavefield(const fdw_solver *s, int level, float *out, int ptr_is_device);
 
 /*
+ * ---- Learned closure ------------------------------------------------------
+ * The paper trades grid spacing against stencil order (Section "Cost-benefit
+ * analysis"); it has no learned part. The closure is a 3x3x3 convolutional
+ * network, 3 -> 16 -> 16 -> 1 channels with ReLU between, that corrects a
+ * coarse low-order time step toward a fine high-order one:
+ *   x = (u_n / s, u_{n-1} / s, (v - 3000 m/s) / 750 m/s),  s = max |u_n|
+ *   over the computational grid (1e-30 if the level is zero),
+ *   x0 = (0, 0, (v - 3000 m/s) / 750 m/s),
+ *   u_{n+1} += s * (net(x) - net(x0))   (applied every coarse step, on the
+ *   physical points only: the sponge keeps the plain update).
+ * The correction vanishes wherever u_n and u_{n-1} vanish over the 7^3
+ * receptive field: an output there would be integrated twice by the
+ * leapfrog update and grow quadratically in time.
+ * The velocity channel is the physical model extended by edge values into
+ * the sponge, zero-padded outside the computational grid like u.
+ * Parameters (fdw_closure_num_params() = 8673 FP32 values, BF16 copies of
+ * the convolution weights used by the kernels, FP32 biases and
+ * accumulation), concatenated:
+ *   W1[16][3][27], b1[16], W2[16][16][27], b2[16], W3[1][16][27], b3[1],
+ * tap t = (a*3 + b)*3 + c for the offsets (a-1, b-1, c-1) along (z, y, x)
+ * (cross-correlation). Training works on batches of cubic patches
+ * [batch][3][S][S][S] (FP32, device) with valid convolutions: the
+ * correction net(x) - net(x0) is [batch][S-6][S-6][S-6]. Calls are ordered
+ * on the closure's stream.
+ */
+typedef struct fdw_closure fdw_closure;
+
+long long fdw_closure_num_params(void);
+
+/* Create a closure with zero parameters on the current device. */
+int fdw_closure_create(fdw_closure **out, void *stream);
+int fdw_closure_destroy(fdw_closure *c);
+
+/* Set (resets the Adam state) / read the FP32 parameters (host or device). */
+int fdw_closure_set_params(fdw_closure *c, const float *params, int ptr_is_device);
+int fdw_closure_get_params(fdw_closure *c, float *params, int ptr_is_device);
+
+/* Correction net(x) - net(x0) of a patch batch: out [batch][S-6]^3 (device). */
+int fdw_closure_forward(fdw_closure *c, const float *x, int batch, int S, float *out);
+
+/*
+ * Mean-squared error of the correction against target [batch][S-6]^3
+ * (device), written to
+ * *loss (device float), and its gradient w.r.t. the parameters into grad
+ * (device, fdw_closure_num_params() floats; NULL for the loss only).
+ * Deterministic: fixed-order reductions, no atomics.
+ */
+int fdw_closure_loss_grad(fdw_closure *c, const float *x, const float *target, int batch, int S,
+                          float *loss, float *grad);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the batch's loss. */
+int fdw_closure_adam_step(fdw_closure *c, const float *x, const float *target, int batch, int S,
+                          float lr, float *loss);
+
+/*
+ * Advance the solver nsteps steps with the closure applied after each
+ * stencil update (acoustic only; the closure and the solver must live on
+ * the same device and their calls are ordered on the solver's stream).
+ * Allocates the closure's inference workspace for the solver's grid on
+ * first use. Errors: INVALID_ARG, STATE (no dt), OOM, CUDA.
+ */
+int fdw_step_closure(fdw_solver *s, fdw_closure *c, int nsteps);
+
+/*
  * Kernel timing. After fdw_profile_begin, up to max_launches (<= 65536)
  * stencil launches issued by fdw_step are bracketed by CUDA events recorded
  * on the solver's stream (steps are then launched individually instead of

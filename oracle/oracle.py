@@ -381,3 +381,89 @@ def closure_loss_grad(params, x, target, hidden=16, grad=True):
     _chk(L.or_closure_loss_grad(hidden, B, nz, ny, nx, _p(params), _p(x), _p(target), _p(loss),
                                 _p(g)), "closure_loss_grad")
     return float(loss[0]), g
+
+
+def closure_forward_same(params, x, hidden=16):
+    """The closure net on a whole grid, as the time loop applies it: every
+    3x3x3 convolution keeps the grid's size and reads zeros outside it.
+    x [3, nz, ny, nx] -> [nz, ny, nx]. Parameter layout as in fdoracle.c
+    (W1[H][3][27], b1, W2[H][H][27], b2, W3[1][H][27], b3; tap (a*3+b)*3+c
+    for offsets (a-1, b-1, c-1) along (z, y, x))."""
+    p = _f64(params)
+    x = _f64(x)
+    H = hidden
+    layers = []
+    off = 0
+    for ci, co in ((3, H), (H, H), (H, 1)):
+        W = p[off:off + co * ci * 27].reshape(co, ci, 27)
+        off += co * ci * 27
+        b = p[off:off + co]
+        off += co
+        layers.append((W, b))
+    a = x
+    for li, (W, b) in enumerate(layers):
+        _, nz, ny, nx = a.shape
+        ap = np.pad(a, ((0, 0), (1, 1), (1, 1), (1, 1)))
+        out = np.broadcast_to(b[:, None, None, None], (W.shape[0], nz, ny, nx)).copy()
+        for ta in range(3):
+            for tb in range(3):
+                for tc in range(3):
+                    tap = (ta * 3 + tb) * 3 + tc
+                    out += np.einsum("oi,izyx->ozyx", W[:, :, tap],
+                                     ap[:, ta:ta + nz, tb:tb + ny, tc:tc + nx])
+        a = np.maximum(out, 0.0) if li < 2 else out
+    return a[0]
+
+
+def closure_correction(params, x, hidden=16):
+    """net(x) - net(x0) of a patch x [3, nz, ny, nx] (valid convolutions),
+    x0 = x with the two wavefield channels set to zero."""
+    x = _f64(x)
+    x0 = x.copy()
+    x0[:2] = 0.0
+    return closure_forward(params, x, hidden) - closure_forward(params, x0, hidden)
+
+
+def closure_correction_loss_grad(params, x, target, hidden=16):
+    """Mean-squared error of net(x) - net(x0) against target for a batch
+    x [B, 3, nz, ny, nx], and its gradient w.r.t. the parameters.
+
+    With r = net(x) - net(x0) - target, the gradient is (2/M) sum r (d net(x)
+    - d net(x0)). Each half is a vector-Jacobian product, obtained from the
+    plain loss gradient: the gradient of mean (net(y) - (net(y) - r))^2 is
+    exactly (2/M) sum r d net(y)."""
+    params, x, target = _f64(params), _f64(x), _f64(target)
+    B = x.shape[0]
+    x0 = x.copy()
+    x0[:, :2] = 0.0
+    f = np.stack([closure_forward(params, x[b], hidden) for b in range(B)])
+    f0 = np.stack([closure_forward(params, x0[b], hidden) for b in range(B)])
+    r = f - f0 - target
+    loss = float(np.mean(r * r))
+    _, g1 = closure_loss_grad(params, x, f - r, hidden)
+    _, g0 = closure_loss_grad(params, x0, f0 - r, hidden)
+    return loss, g1 - g0
+
+
+def closure_step(s: Setup, u, um, vp, params, src_xyz=None, amp=None, hidden=16):
+    """One coarse step with the closure: the acoustic update of Algorithm 1
+    plus m * (net(x) - net(x0)), x = (u_n / m, u_{n-1} / m, (v - 3000) / 750),
+    x0 = (0, 0, (v - 3000) / 750), m = max |u_n| (1e-30 for a zero level),
+    v the physical model extended into the sponge, every convolution
+    zero-padded to the grid's size; the correction is added on the physical
+    points only (the sponge keeps the plain update). Returns u_{n+1}."""
+    u, um = _f64(u), _f64(um)
+    up = acoustic_step(s, u, um)
+    m = float(np.max(np.abs(u)))
+    m = m if m > 1e-30 else 1e-30
+    vn = (extend(vp, s.nb) - 3000.0) / 750.0
+    z = np.zeros_like(u)
+    corr = (closure_forward_same(params, np.stack([u / m, um / m, vn]), hidden)
+            - closure_forward_same(params, np.stack([z, z, vn]), hidden))
+    nb = s.nb
+    inner = tuple(slice(nb, n - nb) for n in u.shape)
+    up[inner] += m * corr[inner]
+    if src_xyz is not None:
+        # the source term alone: a step of zero fields injects exactly it
+        up = up + acoustic_step(s, z, z, src_xyz, amp)
+    return up

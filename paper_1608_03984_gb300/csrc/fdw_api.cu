@@ -997,6 +997,40 @@ extern "C" int fdw_get_adjoint_wavefield(const fdw_solver *cs, int level, float 
   return FDW_OK;
 }
 
+extern "C" int fdw_step_closure(fdw_solver *s, fdw_closure *c, int nsteps) {
+  if (!s || !c) return fail(FDW_ERR_INVALID_ARG, "NULL solver or closure");
+  if (s->eq != FDW_ACOUSTIC) return fail(FDW_ERR_INVALID_ARG, "the closure corrects the acoustic step");
+  if (nsteps < 0) return fail(FDW_ERR_INVALID_ARG, "nsteps < 0");
+  if (!s->dt_set) return fail(FDW_ERR_STATE, "fdw_set_dt must come before fdw_step_closure");
+  DeviceGuard g(s->device);
+  int rc = build_maps(s);
+  if (rc) return rc;
+  CK(acoustic_prepare(s->storage, s->r, s->tile));
+  if (closure_reserve_infer(c, s->d)) return fail(FDW_ERR_OOM, "closure inference workspace");
+  if (nsteps > 0)  // the network's answer for a zero wavefield, subtracted every step
+    CK(closure_infer_base(c, s->vp, s->nx, s->ny, s->nz, s->nb, s->d, s->stream));
+  const size_t fb = s->d.vol() * s->el;
+  for (int n = 0; n < nsteps; ++n) {
+    const int cur = s->cur, nxt = 1 - cur;
+    CK(closure_infer_pre(c, s->storage, s->f[0][cur], s->f[0][nxt], s->vp, s->nx, s->ny, s->nz, s->nb,
+                         s->d, s->stream));
+    rc = enqueue_stencil(s, cur, s->stream);
+    if (rc) return rc;
+    CK(closure_infer_apply(c, s->storage, s->f[0][nxt], s->d, s->nx, s->ny, s->nz, s->nb, s->stream));
+    rc = enqueue_sparse(s, cur, s->stream);
+    if (rc) return rc;
+    s->cur = nxt;
+    if (s->hist_on) {
+      const int lvl = s->it + n + 1, H = (int)s->hist.size();
+      const int slot = ((lvl % H) + H) % H;
+      CK(cudaMemcpyAsync(s->hist[slot], s->f[0][s->cur], fb, cudaMemcpyDeviceToDevice, s->stream));
+      s->hist_level[slot] = lvl;
+    }
+  }
+  s->it += nsteps;
+  return FDW_OK;
+}
+
 extern "C" int fdw_profile_begin(fdw_solver *s, int max_launches) {
   if (!s || max_launches < 1 || max_launches > 65536)
     return fail(FDW_ERR_INVALID_ARG, "max_launches must be in [1, 65536]");

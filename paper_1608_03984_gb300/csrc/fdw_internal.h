@@ -167,6 +167,45 @@ cudaError_t launch_sparse(const SparseLaunch &L, cudaStream_t st);
 // Set the thread-local message of fdw_last_error and return `code`.
 int report_error(int code, const char *fmt, ...);
 
+// Learned closure (closure.cu): parameters and workspaces.
+struct ClosureNet {
+  cudaStream_t stream = nullptr;
+  float *pf = nullptr;            // FP32 master parameters
+  __nv_bfloat16 *pb = nullptr;    // BF16 copy used by the kernels
+  float *grad = nullptr, *m = nullptr, *v = nullptr;  // gradient, Adam moments
+  int adam_t = 0;
+  // training workspace
+  float *a1 = nullptr, *a2 = nullptr, *out = nullptr, *g3 = nullptr, *g2 = nullptr, *g1 = nullptr;
+  float *partial = nullptr, *loss_partial = nullptr;
+  // capacity (points per channel) of the layer-1/2/3 outputs of the workspace
+  size_t cap1 = 0, cap2 = 0, cap3 = 0;
+  float *xpair = nullptr;         // a batch and its zero-wavefield copy
+  size_t xcap = 0;                // floats in xpair
+  // inference workspace (one computational grid); base = net(0, 0, v)
+  float *x = nullptr, *ia1 = nullptr, *ia2 = nullptr, *base = nullptr, *s_dev = nullptr;
+  float *s_partial = nullptr;     // per-block maxima of |u_n|
+  size_t infer_cap = 0;           // points
+};
+// Once per fdw_step_closure call: base = net(0, 0, v) on the grid.
+cudaError_t closure_infer_base(ClosureNet *c, const float *vp, int nx, int ny, int nz, int nb, Dims d,
+                               cudaStream_t st);
+// Before the stencil of a step: s = max |u_n|, inputs, the first two layers.
+cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const void *um,
+                              const float *vp, int nx, int ny, int nz, int nb, Dims d,
+                              cudaStream_t st);
+// After the stencil: u_{n+1} += s * (last layer - base) on the physical
+// points (sponge width nb, physical extents nx, ny, nz).
+cudaError_t closure_infer_apply(ClosureNet *c, int storage, void *unew, Dims d, int nx, int ny, int nz, int nb,
+                                cudaStream_t st);
+int closure_reserve_infer(ClosureNet *c, Dims d);
+
+}  // namespace fdw
+
+// The public closure handle of include/fdwave.h.
+struct fdw_closure : fdw::ClosureNet {};
+
+namespace fdw {
+
 // FWI gradient kernels (adjoint.cu)
 cudaError_t launch_grad_accum(int storage, const void *mu, const void *u1, const void *u0,
                               const void *um1, float *g32, Dims d, Sponge sp, cudaStream_t st);

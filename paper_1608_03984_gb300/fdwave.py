@@ -67,6 +67,15 @@ _SIGS = {
     "fdw_get_adjoint_wavefield": ([_P, _I, _P, _I], _I),
     "fdw_misfit": ([_P, _P, ctypes.c_longlong, _P, _P, _P], _I),
     "fdw_misfit_noalloc": ([_P, _P, ctypes.c_longlong, _P, _P, _P], _I),
+    "fdw_closure_num_params": ([], ctypes.c_longlong),
+    "fdw_closure_create": ([ctypes.POINTER(_P), _P], _I),
+    "fdw_closure_destroy": ([_P], _I),
+    "fdw_closure_set_params": ([_P, _P, _I], _I),
+    "fdw_closure_get_params": ([_P, _P, _I], _I),
+    "fdw_closure_forward": ([_P, _P, _I, _I, _P], _I),
+    "fdw_closure_loss_grad": ([_P, _P, _P, _I, _I, _P, _P], _I),
+    "fdw_closure_adam_step": ([_P, _P, _P, _I, _I, ctypes.c_float, _P], _I),
+    "fdw_step_closure": ([_P, _P, _I], _I),
     "fdw_profile_begin": ([_P, _I], _I),
     "fdw_profile_end": ([_P, ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
 }
@@ -171,6 +180,74 @@ def misfit(d, d_obs, residual=None, J=None, stream=None):
     _chk(lib().fdw_misfit(_cuda_f64(d, "d"), _cuda_f64(d_obs, "d_obs"), n, rp,
                           _cuda_f64(J, "J"), _stream_handle(stream)))
     return J
+
+
+class Closure:
+    """The learned closure network of fdwave.h (3x3x3 convs 3 -> 16 -> 16 -> 1).
+    Batches are float32 CUDA tensors [B, 3, S, S, S]; targets [B, S-6, S-6, S-6]."""
+
+    def __init__(self, stream=None):
+        self.stream = _stream_handle(stream)
+        h = _P()
+        _chk(lib().fdw_closure_create(ctypes.byref(h), self.stream))
+        self._h = h
+        self.num_params = int(lib().fdw_closure_num_params())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fdw_closure_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        ptr, dev, keep = _ptr(p, np.float32)
+        if (keep.numel() if _is_torch(keep) else keep.size) != self.num_params:
+            raise ValueError("expected %d parameters" % self.num_params)
+        _chk(lib().fdw_closure_set_params(self._h, ptr, dev))
+
+    def get_params(self):
+        out = np.zeros(self.num_params, dtype=np.float32)
+        _chk(lib().fdw_closure_get_params(self._h, out.ctypes.data, 0))
+        return out
+
+    @staticmethod
+    def _batch(x):
+        import torch
+        if not (x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.dim() == 5
+                and x.shape[1] == 3 and x.shape[2] == x.shape[3] == x.shape[4]):
+            raise ValueError("x must be a contiguous float32 CUDA tensor [B, 3, S, S, S]")
+        return x.shape[0], x.shape[2]
+
+    def forward(self, x, out=None):
+        import torch
+        B, S = self._batch(x)
+        if out is None:
+            out = torch.empty((B, S - 6, S - 6, S - 6), dtype=torch.float32, device=x.device)
+        _chk(lib().fdw_closure_forward(self._h, x.data_ptr(), B, S, out.data_ptr()))
+        return out
+
+    def loss_grad(self, x, target, grad=True):
+        import torch
+        B, S = self._batch(x)
+        loss = torch.empty((), dtype=torch.float32, device=x.device)
+        g = torch.empty(self.num_params, dtype=torch.float32, device=x.device) if grad else None
+        _chk(lib().fdw_closure_loss_grad(self._h, x.data_ptr(), target.contiguous().data_ptr(), B, S,
+                                         loss.data_ptr(), g.data_ptr() if grad else None))
+        return loss, g
+
+    def adam_step(self, x, target, lr, loss=None):
+        import torch
+        B, S = self._batch(x)
+        if loss is None:
+            loss = torch.empty((), dtype=torch.float32, device=x.device)
+        _chk(lib().fdw_closure_adam_step(self._h, x.data_ptr(), target.contiguous().data_ptr(), B, S,
+                                         float(lr), loss.data_ptr()))
+        return loss
 
 
 class Solver:
@@ -287,6 +364,11 @@ class Solver:
 
     def step(self, n=1):
         _chk(lib().fdw_step(self._h, int(n)))
+        return self
+
+    def step_closure(self, closure, n=1):
+        """n steps with the learned closure applied after every update."""
+        _chk(lib().fdw_step_closure(self._h, closure._h, int(n)))
         return self
 
     def check(self, finite=True):

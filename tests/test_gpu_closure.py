@@ -1,0 +1,262 @@
+"""The learned closure on the GPU: training kernels (forward, loss,
+parameter gradient, Adam) and the closure step of the time loop against the
+FP64 oracle, and the trained network's gain over the coarse solver alone.
+What is compared is the correction net(x) - net(x0) (x0: the same input
+with the wavefield channels zeroed).
+
+The kernels use BF16 copies of the convolution weights (biases stay FP32)
+and accumulate in FP32; the oracle gets the same BF16-rounded weights, so
+the remaining difference is FP32 rounding of sums of at most 16*27 = 432
+products (relative ~1e-6)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+H = 16
+NW = (H * 3 * 27, H, H * H * 27, H, H * 27, 1)  # W1 b1 W2 b2 W3 b3
+
+
+def bf16_weights(p):
+    """Round the convolution weights (not the biases) to BF16, nearest-even."""
+    import torch
+    p = np.asarray(p, dtype=np.float32).copy()
+    i = 0
+    for k, n in enumerate(NW):
+        if k % 2 == 0:
+            p[i:i + n] = torch.from_numpy(p[i:i + n]).to(torch.bfloat16).float().numpy()
+        i += n
+    return p
+
+
+def random_params(seed, scale=1.0):
+    from paper_1608_03984_gb300 import closure
+    p = closure.init_params(seed, last_scale=scale)
+    rng = np.random.default_rng(seed + 1)
+    # non-zero biases exercise the bias gradients
+    i = 0
+    for k, n in enumerate(NW):
+        if k % 2 == 1:
+            p[i:i + n] = 0.1 * rng.standard_normal(n)
+        i += n
+    return bf16_weights(p)
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("B,S", [(1, 7), (3, 10), (8, 18)])
+def test_forward_matches_oracle(fdw, O, torch_mod, B, S):
+    torch = torch_mod
+    p = random_params(B)
+    rng = np.random.default_rng(S)
+    x = rng.standard_normal((B, 3, S, S, S)).astype(np.float32)
+    net = fdw.Closure()
+    net.set_params(p)
+    out = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    for b in range(B):
+        ref = O.closure_correction(p.astype(np.float64), x[b].astype(np.float64))
+        assert rel(out[b], ref) < 1e-5, b
+    net.close()
+
+
+@pytest.mark.parametrize("B,S", [(1, 7), (3, 10), (8, 18)])
+def test_loss_and_gradient_match_oracle(fdw, O, torch_mod, B, S):
+    """Loss and the full parameter gradient (8673 values) of the correction
+    net(x) - net(x0) against the oracle, whose gradient is pinned to central
+    differences."""
+    torch = torch_mod
+    p = random_params(10 + B)
+    rng = np.random.default_rng(20 + S)
+    x = rng.standard_normal((B, 3, S, S, S)).astype(np.float32)
+    t = rng.standard_normal((B, S - 6, S - 6, S - 6)).astype(np.float32)
+    net = fdw.Closure()
+    net.set_params(p)
+    loss, g = net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    ref_loss, ref_g = O.closure_correction_loss_grad(p.astype(np.float64), x.astype(np.float64),
+                                                     t.astype(np.float64))
+    assert abs(float(loss) - ref_loss) <= 2e-6 * ref_loss
+    g = g.cpu().numpy()
+    assert rel(g, ref_g) < 1e-4
+    i = 0
+    # every block of the gradient, not only the bulk; b3's gradient is zero
+    # (it cancels in net(x) - net(x0)), so blocks are measured against the
+    # larger of their own norm and 1e-3 of the whole gradient's
+    for k, n in enumerate(NW):
+        err = np.linalg.norm(g[i:i + n] - ref_g[i:i + n])
+        assert err <= 1e-4 * max(np.linalg.norm(ref_g[i:i + n]), 1e-3 * np.linalg.norm(ref_g)), k
+        i += n
+    net.close()
+
+
+def test_patch_size_changes_on_one_network(fdw, O, torch_mod):
+    """One network fed many small patches, then one large patch (the second
+    needs larger layer buffers although it has fewer input points)."""
+    torch = torch_mod
+    p = random_params(21)
+    net = fdw.Closure()
+    net.set_params(p)
+    rng = np.random.default_rng(22)
+    for B, S in ((8, 9), (1, 18), (2, 11)):
+        x = rng.standard_normal((B, 3, S, S, S)).astype(np.float32)
+        out = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+        for b in range(B):
+            ref = O.closure_correction(p.astype(np.float64), x[b].astype(np.float64))
+            assert rel(out[b], ref) < 1e-5, (B, S, b)
+    net.close()
+
+
+def test_loss_gradient_is_deterministic(fdw, torch_mod):
+    torch = torch_mod
+    p = random_params(3)
+    rng = np.random.default_rng(9)
+    x = torch.from_numpy(rng.standard_normal((6, 3, 16, 16, 16)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((6, 10, 10, 10)).astype(np.float32)).cuda()
+    net = fdw.Closure()
+    net.set_params(p)
+    l1, g1 = net.loss_grad(x, t)
+    l2, g2 = net.loss_grad(x, t)
+    assert torch.equal(l1, l2) and torch.equal(g1, g2)
+    net.close()
+
+
+def test_adam_step_matches_update_rule(fdw, torch_mod):
+    """Two Adam steps recomputed in FP64 from the gradients the library
+    reports at the same parameters (its gradients are deterministic)."""
+    torch = torch_mod
+    p0 = random_params(4)
+    rng = np.random.default_rng(11)
+    x = torch.from_numpy(rng.standard_normal((2, 3, 12, 12, 12)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((2, 6, 6, 6)).astype(np.float32)).cuda()
+    net = fdw.Closure()
+    net.set_params(p0)
+    p = p0.astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    lr = 1e-3
+    for it in (1, 2):
+        _, g = net.loss_grad(x, t)
+        g = g.double().cpu().numpy()
+        net.adam_step(x, t, lr)
+        m = 0.9 * m + 0.1 * g
+        v = 0.999 * v + 0.001 * g * g
+        p = p - lr * (m / (1 - 0.9 ** it)) / (np.sqrt(v / (1 - 0.999 ** it)) + 1e-8)
+        got = net.get_params()
+        np.testing.assert_allclose(got, p, rtol=1e-6, atol=1e-9)
+        p = got.astype(np.float64)  # continue from the library's FP32 parameters
+    net.close()
+
+
+def _coarse_case(fdw, O, seed, storage="f32"):
+    from paper_1608_03984_gb300 import synth
+    n, nb, h, order = 22, 5, 20.0, 4
+    vp = synth.random_velocity((n, n + 2, n + 4), h, 120.0, seed)
+    dt = 0.35 * h / 4500.0
+    solver = fdw.Solver(vp.shape, h, nb, order, storage=storage)
+    # unit storage scale: the O(1) random levels fit FP16's range
+    solver.set_model(vp).set_sponge(4500.0).set_field_scale(1.0).set_dt(dt)
+    src = np.array([[210.0, 190.0, 200.0]])
+    wav = (1e3 * synth.ricker(12.0, dt, 20)).astype(np.float32)
+    solver.set_sources(src, wav.reshape(-1, 1))
+    comp = solver.comp_shape
+    u0 = synth.random_wavefield(comp, seed + 1, smooth_pts=2.0).astype(np.float32)
+    um = synth.random_wavefield(comp, seed + 2, smooth_pts=2.0).astype(np.float32)
+    solver.set_wavefield(u0, 0, 0)
+    solver.set_wavefield(um, 0, 1)
+    setup = O.Setup(vp, h, nb, order, dt, gamma_vmax=4500.0)
+    return solver, setup, vp, src, wav, u0, um
+
+
+def test_step_closure_matches_oracle(fdw, O):
+    """Five coarse steps with the closure (order 4, 22 x 24 x 26 physical,
+    sponge 5, a point source, random initial levels) against the oracle's
+    closure step on the same BF16-rounded weights."""
+    solver, setup, vp, src, wav, u0, um = _coarse_case(fdw, O, 31)
+    p = random_params(7, scale=0.3)
+    net = fdw.Closure()
+    net.set_params(p)
+    ref_u, ref_um = u0.astype(np.float64), um.astype(np.float64)
+    for k in range(5):
+        solver.step_closure(net, 1)
+        nxt = O.closure_step(setup, ref_u, ref_um, vp, p.astype(np.float64), src, [wav[k]])
+        ref_um, ref_u = ref_u, nxt
+        got = solver.wavefield(0, 0)
+        e = rel(got, ref_u)
+        assert e < 1e-5 * (k + 1), (k, e)
+    # the correction is not negligible: plain steps end far from it
+    pu, pum = u0.astype(np.float64), um.astype(np.float64)
+    for k in range(5):
+        pu, pum = O.acoustic_step(setup, pu, pum, src, [wav[k]]), pu
+    assert rel(pu, ref_u) > 1e-2
+    assert solver.current_step == 5
+    net.close()
+    solver.close()
+
+
+def test_step_closure_zero_network_equals_plain_step(fdw, O):
+    """All-zero parameters: fdw_step_closure gives fdw_step's levels."""
+    a, *_ = _coarse_case(fdw, O, 41)
+    b, *_ = _coarse_case(fdw, O, 41)
+    net = fdw.Closure()
+    net.set_params(np.zeros(net.num_params, np.float32))
+    a.step(4)
+    b.step_closure(net, 4)
+    np.testing.assert_array_equal(a.wavefield(0, 0), b.wavefield(0, 0))
+    np.testing.assert_array_equal(a.wavefield(0, 1), b.wavefield(0, 1))
+    net.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_step_closure_16bit_storage(fdw, O, storage):
+    """16-bit wavefield storage: the closure reads and updates the stored
+    levels; three steps stay within the storage rounding of the oracle."""
+    solver, setup, vp, src, wav, u0, um = _coarse_case(fdw, O, 51, storage)
+    p = random_params(8, scale=0.3)
+    net = fdw.Closure()
+    net.set_params(p)
+    ref_u, ref_um = solver.wavefield(0, 0).astype(np.float64), solver.wavefield(0, 1).astype(np.float64)
+    for k in range(3):
+        solver.step_closure(net, 1)
+        nxt = O.closure_step(setup, ref_u, ref_um, vp, p.astype(np.float64), src, [wav[k]])
+        ref_um, ref_u = ref_u, nxt
+    tol = {"bf16": 3e-2, "f16": 4e-3}[storage]
+    assert rel(solver.wavefield(0, 0), ref_u) < tol
+    net.close()
+    solver.close()
+
+
+def test_training_reduces_error_on_held_out_models(fdw):
+    """Train on solver-generated pairs from ten random models (fine order 16
+    at h = 10 m, coarse order 4 at h = 20 m, 96^3 coarse physical points,
+    a 10 Hz Ricker source at the centre, steps after the source has ended),
+    then on four held-out models the coarse run with the closure is closer
+    to the restricted fine run than the coarse run alone: in the final
+    wavefield and in the receiver traces, for every model, and by at least
+    15% on average."""
+    from paper_1608_03984_gb300 import closure as C
+    pr = C.Pairing(n_c=96, nb_c=8, src_sigma=1.5)
+    nt = pr.steps_to_cross(0.45)
+    samplers = []
+    for seed in range(100, 110):
+        x, t = C.samples(pr, seed, nt, stride=2)
+        samplers.append(C.PatchSampler(x, t, P=12, nb=pr.nb_c))
+    net = fdw.Closure()
+    losses = C.train(net, samplers, iters=8000, batch=32, lr=3e-3)
+    assert losses[-1] < 0.5 * losses[0]
+    ratios = {"field": [], "traces": []}
+    for seed in (900, 901, 902, 903):
+        r = C.evaluate(pr, net, seed, nt)
+        for key in ratios:
+            assert r["closure"][key] < r["coarse"][key], (seed, r)
+            ratios[key].append(r["closure"][key] / r["coarse"][key])
+    for key, v in ratios.items():
+        assert np.mean(v) < 0.85, (key, v)
+    net.close()
