@@ -57,6 +57,12 @@ def parse():
     p.add_argument("--fwi-nt", type=int, default=2000)
     p.add_argument("--fwi-shots-side", type=int, default=4)
     p.add_argument("--tti-n", type=int, default=384, help="physical TTI grid points per axis")
+    p.add_argument("--no-closure", action="store_true")
+    p.add_argument("--closure-n", type=int, default=256, help="coarse physical points per axis (evaluation)")
+    p.add_argument("--closure-train-n", type=int, default=96, help="coarse points per axis (training models)")
+    p.add_argument("--closure-models", type=int, default=10)
+    p.add_argument("--closure-iters", type=int, default=8000)
+    p.add_argument("--closure-eval", type=int, default=2, help="held-out models at full size")
     return p.parse_args()
 
 
@@ -357,6 +363,10 @@ def run_fdwave(args, orders):
     if not args.no_fwi and world == 1:
         fwi_res = run_fwi(args)
 
+    closure_res = None
+    if not args.no_closure and world == 1:
+        closure_res = run_closure(args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         samples = [oracle_sample(base.vp, base.h, base.nb, o, base.dt) for o in orders]
@@ -382,7 +392,7 @@ def run_fdwave(args, orders):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_dict(args, orders, base),
             "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu, "tti": tti,
-            "fwi": fwi_res, "storage": storage, "paper_model_gb300": paper,
+            "fwi": fwi_res, "storage": storage, "closure": closure_res, "paper_model_gb300": paper,
             "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
         }
         print(json.dumps(line), flush=True)
@@ -527,6 +537,59 @@ def run_fwi(args):
             "stencil_steps": 3 * w.nt * nshot,
             "gpts_equiv": 3 * w.nt * nshot * pts / sec / 1e9,
             "gradient_finite": bool(torch.isfinite(g).all())}
+
+
+def run_closure(args):
+    """The learned closure: fine order 16 at h = 10 m vs coarse order 4 at
+    h = 20 m (coarse point i = fine point 2i, dt_c = 2 dt_f), 10 Hz Ricker
+    at the centre. Trained (library kernels) on restricted fine runs of
+    smaller random models of the same spacing and statistics (the network
+    is local: 7^3 receptive field), evaluated on held-out models at full
+    size: relative L2 error against the restricted fine run with and without
+    the closure, and device time of each run (CUDA events)."""
+    import numpy as np
+    import torch
+    from paper_1608_03984_gb300 import closure as C, fdwave
+    tr = C.Pairing(n_c=args.closure_train_n, nb_c=8, src_sigma=1.5)
+    nt_tr = tr.steps_to_cross(0.45)
+    t0 = time.perf_counter()
+    samplers = []
+    for seed in range(5000, 5000 + args.closure_models):
+        x, t = C.samples(tr, seed, nt_tr, stride=2)
+        samplers.append(C.PatchSampler(x, t, P=12, nb=tr.nb_c))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    net = fdwave.Closure()
+    losses = C.train(net, samplers, iters=args.closure_iters, batch=32, lr=3e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    held = C.PatchSampler(*C.samples(tr, 5064, nt_tr, stride=2), P=12, nb=tr.nb_c)
+    unexpl = {"train": C.unexplained(net, samplers[0]), "held_out": C.unexplained(net, held)}
+    del samplers, held
+    torch.cuda.empty_cache()
+    pr = C.Pairing(n_c=args.closure_n, nb_c=20, src_sigma=1.5)
+    nt = pr.steps_to_cross(0.45)
+    evals = []
+    for seed in range(5064, 5064 + args.closure_eval):
+        r = C.evaluate(pr, net, seed, nt, timing=True)
+        evals.append(r)
+    net.close()
+    ms = {k: float(np.mean([r["ms"][k] for r in evals])) for k in ("fine", "coarse", "closure")}
+    err = {m: {k: float(np.mean([r[m][k] for r in evals])) for k in ("field", "traces")}
+           for m in ("coarse", "closure")}
+    k1 = pr.source_steps()
+    return {"workload": "fine %d^3 + %d-pt sponge h=%g order %d, %d steps; coarse %d^3 + %d-pt sponge "
+                        "h=%g order %d, %d steps (closure after step %d); %d held-out models; trained "
+                        "on %d models of %d^3 coarse points" % (
+                            pr.n_f, pr.nb_f, pr.h_f, pr.order_f, 2 * nt, pr.n_c, pr.nb_c, pr.h_c,
+                            pr.order_c, nt, k1, args.closure_eval, args.closure_models, tr.n_c),
+            "error_vs_fine": err, "ms": ms,
+            "speedup_vs_fine": {"coarse": ms["fine"] / ms["coarse"], "closure": ms["fine"] / ms["closure"]},
+            "closure_ms_per_step": (ms["closure"] - ms["coarse"] * k1 / nt) / (nt - k1),
+            "coarse_ms_per_step": ms["coarse"] / nt,
+            "one_step_unexplained": unexpl, "train_loss_first_last": [losses[0], losses[-1]],
+            "data_s": t1 - t0, "train_s": t2 - t1, "iters": args.closure_iters,
+            "per_model": [{"coarse": r["coarse"], "closure": r["closure"]} for r in evals]}
 
 
 def run_e2e(args, orders, base, stream):

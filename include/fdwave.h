@@ -327,7 +327,8 @@ int fdw_get_adjoint_wavefield(const fdw_solver *s, int level, float *out, int pt
  *   over the computational grid (1e-30 if the level is zero),
  *   x0 = (0, 0, (v - 3000 m/s) / 750 m/s),
  *   u_{n+1} += s * (net(x) - net(x0))   (applied every coarse step, on the
- *   physical points only: the sponge keeps the plain update).
+ *   physical points 3 or more points away from the sponge, so that the
+ *   7^3 receptive field is physical; elsewhere the plain update stands).
  * The correction vanishes wherever u_n and u_{n-1} vanish over the 7^3
  * receptive field: an output there would be integrated twice by the
  * leapfrog update and grow quadratically in time.

@@ -451,7 +451,8 @@ def closure_step(s: Setup, u, um, vp, params, src_xyz=None, amp=None, hidden=16)
     x0 = (0, 0, (v - 3000) / 750), m = max |u_n| (1e-30 for a zero level),
     v the physical model extended into the sponge, every convolution
     zero-padded to the grid's size; the correction is added on the physical
-    points only (the sponge keeps the plain update). Returns u_{n+1}."""
+    points whose 7^3 receptive field is physical (3 points or more from the
+    sponge); elsewhere the plain update stands. Returns u_{n+1}."""
     u, um = _f64(u), _f64(um)
     up = acoustic_step(s, u, um)
     m = float(np.max(np.abs(u)))
@@ -460,8 +461,8 @@ def closure_step(s: Setup, u, um, vp, params, src_xyz=None, amp=None, hidden=16)
     z = np.zeros_like(u)
     corr = (closure_forward_same(params, np.stack([u / m, um / m, vn]), hidden)
             - closure_forward_same(params, np.stack([z, z, vn]), hidden))
-    nb = s.nb
-    inner = tuple(slice(nb, n - nb) for n in u.shape)
+    a = s.nb + 3
+    inner = tuple(slice(a, n - a) for n in u.shape)
     up[inner] += m * corr[inner]
     if src_xyz is not None:
         # the source term alone: a step of zero fields injects exactly it

@@ -198,10 +198,10 @@ def samples(pr: Pairing, seed: int, nt_c: int, k0: int | None = None, stride: in
 
 
 class PatchSampler:
-    """Random cubic patches of one (x, target) set: targets P^3 on physical
-    points (the closure leaves the sponge alone), inputs (P+6)^3 inside the
-    grid, so that the valid convolutions of a patch give exactly what the
-    time loop's zero-padded ones give there. Every time step (sample) is
+    """Random cubic patches of one (x, target) set: inputs (P+6)^3 on
+    physical points, targets the central P^3 (the points the closure
+    corrects: 3 or more points from the sponge). The valid convolutions of
+    a patch give exactly what the time loop's zero-padded ones give there. Every time step (sample) is
     drawn equally often (the defect while the source acts is ~10x the later
     propagation defect and would otherwise crowd it out); within a step the
     origin is drawn with probability proportional to the patch's defect
@@ -209,8 +209,8 @@ class PatchSampler:
 
     def __init__(self, x, t, P, nb, floor=0.2):
         self.P, self.N = P, x.shape[2]
-        self.lo = max(nb - 3, 0)                    # first input origin
-        side = self.N - nb - P - 3 + 1 - self.lo    # origins o: o + 3 >= nb, o + 3 + P <= N - nb
+        self.lo = nb                                # first input origin
+        side = self.N - 2 * nb - (P + 6) + 1        # origins o: o >= nb, o + P + 6 <= N - nb
         if side < 1:
             raise ValueError("physical region smaller than a patch")
         self.side = side

@@ -30,6 +30,7 @@ constexpr int kOffW1 = 0, kOffB1 = kH * 3 * 27, kOffW2 = kOffB1 + kH, kOffB2 = k
               kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * 27, kNumParams = kOffB3 + 1;
 constexpr float kVelMean = 3000.f, kVelScale = 750.f;
 constexpr int kBwdChunks = 16;  // partial sums per weight-gradient pair
+constexpr int kHalo = 3;        // receptive-field radius of the three 3x3x3 layers
 
 // ---------------------------------------------------------------------------
 // convolutions
@@ -341,9 +342,10 @@ __global__ void closure_inputs_kernel(const T *__restrict__ u, const T *__restri
 }
 
 // Last layer fused with the update: u_{n+1} += s * (b3 + sum W3 a2 - base)
-// on the physical points [nb, nb + n) of each axis; the sponge keeps the
-// plain update (its job is absorption, which the fine solver does not
-// define on the coarse grid).
+// on the physical points whose 7^3 receptive field is physical too:
+// [nb + 3, nb + n - 3) along each axis. The sponge and the 3 points next
+// to it keep the plain update: the sponge's job is absorption, which the
+// fine solver does not define on the coarse grid.
 template <typename T>
 __global__ void __launch_bounds__(256)
     closure_apply_kernel(const float *__restrict__ a2, const __nv_bfloat16 *__restrict__ w3,
@@ -360,7 +362,9 @@ __global__ void __launch_bounds__(256)
     const int x = (int)(q % d.NX);
     const long long r = q / d.NX;
     const int y = (int)(r % d.NY), z = (int)(r / d.NY);
-    if (x < nb || x >= nb + nx || y < nb || y >= nb + ny || z < nb || z >= nb + nz) continue;
+    if (x < nb + kHalo || x >= nb + nx - kHalo || y < nb + kHalo || y >= nb + ny - kHalo ||
+        z < nb + kHalo || z >= nb + nz - kHalo)
+      continue;
     float acc = b3[0];
     for (int a = 0; a < 3; ++a) {
       const int zz = z + a - 1;
