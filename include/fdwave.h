@@ -207,9 +207,10 @@ int fdw_set_kernel_variant(fdw_solver *s, int variant);
 int fdw_set_zchunks(fdw_solver *s, int zchunks);
 
 /*
- * Tile configuration of the 2.5D acoustic kernel (points per thread in x/y,
- * warps per CTA, z unrolling; see acoustic_kernel.cuh): 0..4, or -1 for the
- * default of the solver's order and storage. Resets zchunks to its default.
+ * Tile configuration of the 2.5D kernel: acoustic (points per thread in x/y,
+ * warps per CTA, z unrolling; acoustic_kernel.cuh) or TTI (warps per CTA, z
+ * unrolling; tti_kernel.cuh), 0..4, or -1 for the default of the solver's
+ * equation, order and storage. Resets zchunks to its default.
  * fdw_get_tile_config returns the configuration in use (-1 for NULL).
  * Errors: INVALID_ARG.
  */

@@ -217,7 +217,7 @@ int make_map(CUtensorMap *m, const fdw_solver *s, void *base, int bx, int by) {
 int build_maps(fdw_solver *s) {
   if (s->maps_ok) return FDW_OK;
   TileGeom tg;
-  const int bad = s->eq == FDW_TTI ? tti_geom(s->storage, s->r, &tg)
+  const int bad = s->eq == FDW_TTI ? tti_geom(s->storage, s->r, s->tile, &tg)
                                    : acoustic_geom(s->storage, s->r, s->tile, &tg);
   if (bad) return fail(FDW_ERR_INVALID_ARG, "bad tile");
   const int bhx = tg.box_halo_x, bhy = tg.box_halo_y, bix = tg.box_int_x, biy = tg.box_int_y;
@@ -256,7 +256,7 @@ int min_zchunks(const fdw_solver *s) { return (s->d.NZ + kMaxZChunk - 1) / kMaxZ
 
 int default_zchunks(const fdw_solver *s) {
   TileGeom tg;
-  const int bad = s->eq == FDW_TTI ? tti_geom(s->storage, s->r, &tg)
+  const int bad = s->eq == FDW_TTI ? tti_geom(s->storage, s->r, s->tile, &tg)
                                    : acoustic_geom(s->storage, s->r, s->tile, &tg);
   if (bad) return 1;
   const int bix = tg.box_int_x, biy = tg.box_int_y;
@@ -320,6 +320,7 @@ int enqueue_stencil(fdw_solver *s, int cur, cudaStream_t st) {
     L.zchunks = s->zchunks;
     L.err = s->d_err;
     L.naive = s->naive;
+    L.tile = s->tile;
     CK(launch_tti(L, st));
   }
   return FDW_OK;
@@ -503,7 +504,7 @@ extern "C" int fdw_create(fdw_solver **out, int nx, int ny, int nz, double h, in
     fdw_destroy(s);
     return rc;
   }
-  s->tile = acoustic_default_tile(storage, s->r);
+  s->tile = s->eq == FDW_TTI ? tti_default_tile(storage, s->r) : acoustic_default_tile(storage, s->r);
   s->zchunks = default_zchunks(s);
   const char *nv = getenv("FDW_KERNEL");
   s->naive = (nv && strcmp(nv, "naive") == 0) ? 1 : 0;
@@ -711,7 +712,8 @@ static int ensure_graphs(fdw_solver *s) {
   int rc = build_maps(s);
   if (rc) return rc;
   // kernel attributes (large dynamic shared memory) are set outside capture
-  CK(s->eq == FDW_ACOUSTIC ? acoustic_prepare(s->storage, s->r, s->tile) : tti_prepare(s->storage, s->r));
+  CK(s->eq == FDW_ACOUSTIC ? acoustic_prepare(s->storage, s->r, s->tile)
+                           : tti_prepare(s->storage, s->r, s->tile));
   for (int b = 0; b < 2; ++b) {
     cudaGraph_t gr = nullptr;
     CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
@@ -1192,10 +1194,12 @@ extern "C" int fdw_set_kernel_variant(fdw_solver *s, int variant) {
 extern "C" int fdw_set_tile_config(fdw_solver *s, int tile) {
   if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
   TileGeom tg;
-  if (tile < -1 || tile >= kAcTiles ||
-      (tile >= 0 && acoustic_geom(s->storage, s->r, tile, &tg)))
-    return fail(FDW_ERR_INVALID_ARG, "tile configuration must be -1 (default) or 0..%d", kAcTiles - 1);
-  s->tile = tile < 0 ? acoustic_default_tile(s->storage, s->r) : tile;
+  const bool tti = s->eq == FDW_TTI;
+  const int ntiles = tti ? kTtiTilesMax : kAcTiles;
+  if (tile < -1 || tile >= ntiles ||
+      (tile >= 0 && (tti ? tti_geom(s->storage, s->r, tile, &tg) : acoustic_geom(s->storage, s->r, tile, &tg))))
+    return fail(FDW_ERR_INVALID_ARG, "tile configuration must be -1 (default) or 0..%d", ntiles - 1);
+  s->tile = tile >= 0 ? tile : tti ? tti_default_tile(s->storage, s->r) : acoustic_default_tile(s->storage, s->r);
   s->maps_ok = false;
   s->zchunks = default_zchunks(s);
   drop_graphs(s);

@@ -116,19 +116,22 @@ struct TTILaunch {
   int *err;
   int naive;
   int prepare_only;
+  int tile;           // configuration index of the 2.5D kernel (tti_kernel.cuh)
   // tensor maps: halo tiles of p, r at level n; interior tiles of p, r at
   // level n-1 and of the medium fields
   const CUtensorMap *m_ph, *m_rh, *m_pm, *m_rm, *m_c, *m_e, *m_d, *m_ax, *m_ay;
 };
+constexpr int kTtiTilesMax = 5;  // number of TTI configurations (see tti_kernel.cuh)
 cudaError_t launch_tti(const TTILaunch &L, cudaStream_t st);
-cudaError_t tti_prepare(int storage, int r);
-int tti_geom(int storage, int r, TileGeom *g);
+cudaError_t tti_prepare(int storage, int r, int tile);
+int tti_geom(int storage, int r, int tile, TileGeom *g);
+int tti_default_tile(int storage, int r);
 cudaError_t launch_tti_tma_f32(const TTILaunch &L, cudaStream_t st);
 cudaError_t launch_tti_tma_bf16(const TTILaunch &L, cudaStream_t st);
 cudaError_t launch_tti_tma_f16(const TTILaunch &L, cudaStream_t st);
-int tti_geom_f32(int r, TileGeom *g);
-int tti_geom_bf16(int r, TileGeom *g);
-int tti_geom_f16(int r, TileGeom *g);
+int tti_geom_f32(int r, int tile, TileGeom *g);
+int tti_geom_bf16(int r, int tile, TileGeom *g);
+int tti_geom_f16(int r, int tile, TileGeom *g);
 
 // Sparse work of one step (after the stencil update):
 //   inject: u+ += c w_corner amp / (h P) at each source corner (both p and r

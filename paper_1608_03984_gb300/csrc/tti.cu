@@ -117,20 +117,29 @@ cudaError_t launch_tti(const TTILaunch &L, cudaStream_t st) {
   }
 }
 
-int tti_geom(int storage, int r, TileGeom *g) {
+int tti_geom(int storage, int r, int tile, TileGeom *g) {
   switch (storage) {
-    case FDW_F32: return tti_geom_f32(r, g);
-    case FDW_BF16: return tti_geom_bf16(r, g);
-    case FDW_F16: return tti_geom_f16(r, g);
+    case FDW_F32: return tti_geom_f32(r, tile, g);
+    case FDW_BF16: return tti_geom_bf16(r, tile, g);
+    case FDW_F16: return tti_geom_f16(r, tile, g);
     default: return -1;
   }
 }
 
-cudaError_t tti_prepare(int storage, int r) {
+// Default configuration: four warps per CTA (measured on the 464^3 TTI
+// workload: 4 warps beat 2 and 8), z unrolling 4 up to order 8, 2 at
+// orders 10-12, 1 above (the queues of 6 fields grow with the order).
+int tti_default_tile(int storage, int r) {
+  (void)storage;
+  return r <= 4 ? 1 : r <= 6 ? 2 : 4;
+}
+
+cudaError_t tti_prepare(int storage, int r, int tile) {
   TTILaunch L{};
   memset(&L, 0, sizeof L);
   L.storage = storage;
   L.r = r;
+  L.tile = tile;
   L.prepare_only = 1;
   return launch_tti(L, 0);
 }

@@ -27,8 +27,12 @@
 // (n n^T does not depend on the sign of n).
 //
 // Each TMA stage holds: the p and r halo tiles and the (nx, ny) tiles of the
-// head plane; the p-, r-, c, e, d, nx, ny tiles of the output plane. Every
-// mbarrier wait is bounded (error flag, drain, exit).
+// head plane; the p-, r-, c, e, d, nx, ny tiles of the output plane. The
+// D_y scratch is double-buffered and the cross term D_x(D_y f) of a head
+// plane is finished one iteration later, so one CTA barrier per plane (the
+// ring's) orders both the stage reuse and the scratch. The D_y of the x
+// halo columns is spread evenly over the warps. Every mbarrier wait is
+// bounded (error flag, drain, exit).
 #pragma once
 
 #include "fdw_internal.h"
@@ -53,7 +57,9 @@ struct TtiTile {
   static constexpr int N_INT = 9;
   static constexpr int STAGE_B = 2 * HALO_B + N_INT * INT_B;
   static constexpr int SY = TX + 2 * R;  // row length of the D_y scratch
-  static constexpr int SCR_B = a128(2 * TY * SY * 4);
+  static constexpr int SCR_B = a128(2 * 2 * TY * SY * 4);  // [buffer][field][TY][SY]
+  static constexpr int NHALO = 2 * 2 * R * TY;               // D_y halo items per plane
+  static constexpr int HPW = (NHALO + BY - 1) / BY;          // items per warp
   static constexpr int BAR_B = 128;
   static constexpr int SMEM_B = NS * STAGE_B + SCR_B + BAR_B + kMaxZChunk * 4 + 128;
   static constexpr int THREADS = 32 * BY;
@@ -63,7 +69,7 @@ struct TtiTile {
   static_assert(BXH <= 256 && BYH <= 256, "TMA box dimension limit");
   static_assert((BXH * EL) % 16 == 0 && (TX * EL) % 16 == 0 && (HX * EL) % 16 == 0, "TMA alignment");
   static_assert(SMEM_B <= 227 * 1024, "shared memory per CTA");
-  static_assert(2 * 2 * R * TY <= THREADS * 4, "halo columns of D_y per thread");
+  static_assert(HPW <= 32, "one D_y halo item per lane");
 };
 
 template <typename T, int R, int BY, int NS, int U>
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(32 * BY)
   using C = TtiTile<T, R, BY, NS, U>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  float *scr = (float *)(smem + NS * C::STAGE_B);  // [2][TY][SY] D_y of p and r
+  float *scr = (float *)(smem + NS * C::STAGE_B);  // [2][2][TY][SY] D_y of p and r
   uint64_t *bars = (uint64_t *)(smem + NS * C::STAGE_B + C::SCR_B);
   float *gzs = (float *)(smem + NS * C::STAGE_B + C::SCR_B + C::BAR_B);
 
@@ -148,6 +154,10 @@ __global__ void __launch_bounds__(32 * BY)
 
   const size_t plane = d.plane();
   const int li = ty * C::TX + tx;  // index inside an interior tile
+  // in-plane second derivatives and axis of the previous head plane, whose
+  // cross term is finished one iteration later
+  float pfxx[2] = {0.f, 0.f}, pfyy[2] = {0.f, 0.f}, phx = 0.f, phy = 0.f;
+  bool phead = false;
 
 #pragma unroll 1
   for (int j0 = 0; j0 < nit; j0 += U) {
@@ -157,6 +167,8 @@ __global__ void __launch_bounds__(32 * BY)
       if (j >= nit) break;  // uniform
       const int s = j % NS;
       const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((j / NS) & 1));
+      // Also the point where every thread has finished iteration j-1 (its
+      // stage reads and its D_y scratch writes).
       if (__syncthreads_or(!ok)) {
         if (tid == 0) {
           atomicOr(err, kErrWaitTimeout);
@@ -167,11 +179,33 @@ __global__ void __launch_bounds__(32 * BY)
       }
       if (tid == 0 && j >= 1 && j - 1 + NS < nit) issue(j - 1 + NS);
 
+      // finish head plane j-1: D_x(D_y f) from scratch buffer (j-1)&1, then
+      // its in-plane sums into the delay queue (slot R+u-1; for u = 0 that
+      // is the previous group's last slot after the shift)
+      if (j >= 1) {
+        float a0 = 0.f, a1 = 0.f;
+        if (phead) {
+          float A[2];
+#pragma unroll
+          for (int f = 0; f < 2; ++f) {
+            const float *sr = scr + (((j - 1) & 1) * 2 * C::TY + f * C::TY + ty) * C::SY + R + tx;
+            float xy = 0.f;
+#pragma unroll
+            for (int m = 1; m <= R; ++m) xy = fmaf(w.c1[m], sr[m] - sr[-m], xy);
+            A[f] = phx * phx * pfxx[f] + phy * phy * pfyy[f] + 2.f * phx * phy * xy;
+          }
+          a0 = pfxx[0] + pfyy[0] - A[0];
+          a1 = A[1];
+        }
+        dq[0][R + u - 1] = a0;
+        dq[1][R + u - 1] = a1;
+      }
+
       const unsigned char *st = smem + s * C::STAGE_B;
       const int zh = z0 - R + j;
       const bool head = (zh >= 0 && zh < d.NZ);
+      float *sb = scr + (j & 1) * 2 * C::TY * C::SY;
       if (head) {
-        float fxx[2], fyy[2];
 #pragma unroll
         for (int f = 0; f < 2; ++f) {
           const T *H = (const T *)(st + f * C::HALO_B);
@@ -187,48 +221,40 @@ __global__ void __launch_bounds__(32 * BY)
             yy = fmaf(w.w2[m], yp + ym, yy);
             dy = fmaf(w.c1[m], yp - ym, dy);
           }
-          fxx[f] = xx;
-          fyy[f] = yy;
+          pfxx[f] = xx;
+          pfyy[f] = yy;
           q[3 * f + 0][2 * R + u] = fc;
           q[3 * f + 1][2 * R + u] = dx;
           q[3 * f + 2][2 * R + u] = dy;
-          scr[(f * C::TY + ty) * C::SY + R + tx] = dy;
+          sb[(f * C::TY + ty) * C::SY + R + tx] = dy;
         }
-        // D_y of both fields in the x halo columns [-R, 0) and [32, 32 + R)
-        for (int t = tid; t < 2 * 2 * R * C::TY; t += C::THREADS) {
-          const int f = t / (2 * R * C::TY);
-          const int rem = t - f * (2 * R * C::TY);
-          const int yy_ = rem / (2 * R);
-          const int k = rem - yy_ * (2 * R);
-          const int xo = k < R ? k - R : C::TX + (k - R);  // tile x of the halo column
-          const T *H = (const T *)(st + f * C::HALO_B);
-          const T *col = H + (yy_ + R) * C::BXH + C::HX + xo;
-          float dy = 0.f;
+        // D_y of both fields in the x halo columns [-R, 0) and [32, 32 + R):
+        // HPW items per warp, one per lane
+        if (tx < C::HPW) {
+          const int t = ty * C::HPW + tx;
+          if (t < C::NHALO) {
+            const int f = t / (2 * R * C::TY);
+            const int rem = t - f * (2 * R * C::TY);
+            const int yy_ = rem / (2 * R);
+            const int k = rem - yy_ * (2 * R);
+            const int xo = k < R ? k - R : C::TX + (k - R);  // tile x of the halo column
+            const T *H = (const T *)(st + f * C::HALO_B);
+            const T *col = H + (yy_ + R) * C::BXH + C::HX + xo;
+            float dy = 0.f;
 #pragma unroll
-          for (int m = 1; m <= R; ++m)
-            dy = fmaf(w.c1[m], St<T>::ld(col[m * C::BXH]) - St<T>::ld(col[-m * C::BXH]), dy);
-          scr[(f * C::TY + yy_) * C::SY + R + xo] = dy;
+            for (int m = 1; m <= R; ++m)
+              dy = fmaf(w.c1[m], St<T>::ld(col[m * C::BXH]) - St<T>::ld(col[-m * C::BXH]), dy);
+            sb[(f * C::TY + yy_) * C::SY + R + xo] = dy;
+          }
         }
-        __syncthreads();
         const T *HA = (const T *)(st + 2 * C::HALO_B);
-        const float hx = St<T>::ld(HA[li]), hy = St<T>::ld(HA[C::INT_B / C::EL + li]);
-        float A[2];
-#pragma unroll
-        for (int f = 0; f < 2; ++f) {
-          const float *sr = scr + (f * C::TY + ty) * C::SY + R + tx;
-          float xy = 0.f;
-#pragma unroll
-          for (int m = 1; m <= R; ++m) xy = fmaf(w.c1[m], sr[m] - sr[-m], xy);
-          A[f] = hx * hx * fxx[f] + hy * hy * fyy[f] + 2.f * hx * hy * xy;
-        }
-        dq[0][R + u] = fxx[0] + fyy[0] - A[0];
-        dq[1][R + u] = A[1];
+        phx = St<T>::ld(HA[li]);
+        phy = St<T>::ld(HA[C::INT_B / C::EL + li]);
       } else {
 #pragma unroll
         for (int a = 0; a < 6; ++a) q[a][2 * R + u] = 0.f;
-        dq[0][R + u] = 0.f;
-        dq[1][R + u] = 0.f;
       }
+      phead = head;
       if (j < 2 * R) continue;
 
       // output plane zo = zh - R
@@ -281,16 +307,21 @@ __global__ void __launch_bounds__(32 * BY)
 namespace fdw {
 
 constexpr int kTtiNS = 4;
-constexpr int kTtiU = 2;
-template <int R> struct TtiCfg {
-  static constexpr int BY = 8;
-};
 
-template <typename T, int R>
-cudaError_t launch_tti_tma(const TTILaunch &L, cudaStream_t st) {
-  constexpr int BY = TtiCfg<R>::BY;
-  using C = TtiTile<T, R, BY, kTtiNS, kTtiU>;
-  auto kern = tti_tma_kernel<T, R, BY, kTtiNS, kTtiU>;
+// Candidate configurations (warps per CTA = tile rows BY, z unrolling U),
+// selected at run time by index.
+#define FDW_TTI_CFGS(X) \
+  X(0, 8, 2)            \
+  X(1, 4, 4)            \
+  X(2, 4, 2)            \
+  X(3, 2, 2)            \
+  X(4, 4, 1)
+constexpr int kTtiTiles = 5;
+
+template <typename T, int R, int BY, int U>
+cudaError_t launch_tti_cfg(const TTILaunch &L, cudaStream_t st) {
+  using C = TtiTile<T, R, BY, kTtiNS, U>;
+  auto kern = tti_tma_kernel<T, R, BY, kTtiNS, U>;
   if (L.prepare_only)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_B);
   const int zch = L.zchunks < 1 ? 1 : L.zchunks;
@@ -304,9 +335,9 @@ cudaError_t launch_tti_tma(const TTILaunch &L, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int R>
-void tti_geom_r(TileGeom *g) {
-  using C = TtiTile<T, R, TtiCfg<R>::BY, kTtiNS, kTtiU>;
+template <typename T, int R, int BY, int U>
+void tti_geom_cfg(TileGeom *g) {
+  using C = TtiTile<T, R, BY, kTtiNS, U>;
   g->box_halo_x = C::BXH;
   g->box_halo_y = C::BYH;
   g->box_int_x = C::TX;
@@ -314,30 +345,49 @@ void tti_geom_r(TileGeom *g) {
   g->smem = C::SMEM_B;
 }
 
+#define FDW_TTI_CASE_LAUNCH(ID, BY, U) \
+  case ID: return launch_tti_cfg<TYPE_, R, BY, U>(L, st);
+#define FDW_TTI_CASE_GEOM(ID, BY, U) \
+  case ID: tti_geom_cfg<TYPE_, R, BY, U>(g); return 0;
+
 #define FDW_TTI_DEFINE_STORAGE(SUFFIX, TYPE)                                  \
-  cudaError_t launch_tti_tma_##SUFFIX(const TTILaunch &L, cudaStream_t st) {  \
-    switch (L.r) {                                                            \
-      case 1: return launch_tti_tma<TYPE, 1>(L, st);                          \
-      case 2: return launch_tti_tma<TYPE, 2>(L, st);                          \
-      case 3: return launch_tti_tma<TYPE, 3>(L, st);                          \
-      case 4: return launch_tti_tma<TYPE, 4>(L, st);                          \
-      case 5: return launch_tti_tma<TYPE, 5>(L, st);                          \
-      case 6: return launch_tti_tma<TYPE, 6>(L, st);                          \
-      case 7: return launch_tti_tma<TYPE, 7>(L, st);                          \
-      case 8: return launch_tti_tma<TYPE, 8>(L, st);                          \
+  template <typename TYPE_, int R>                                            \
+  static cudaError_t tti_r_##SUFFIX(const TTILaunch &L, cudaStream_t st) {    \
+    switch (L.tile) {                                                         \
+      FDW_TTI_CFGS(FDW_TTI_CASE_LAUNCH)                                       \
       default: return cudaErrorInvalidValue;                                  \
     }                                                                         \
   }                                                                           \
-  int tti_geom_##SUFFIX(int r, TileGeom *g) {                                 \
+  template <typename TYPE_, int R>                                            \
+  static int tti_geom_r_##SUFFIX(int tile, TileGeom *g) {                     \
+    switch (tile) {                                                           \
+      FDW_TTI_CFGS(FDW_TTI_CASE_GEOM)                                         \
+      default: return -1;                                                     \
+    }                                                                         \
+  }                                                                           \
+  cudaError_t launch_tti_tma_##SUFFIX(const TTILaunch &L, cudaStream_t st) {  \
+    switch (L.r) {                                                            \
+      case 1: return tti_r_##SUFFIX<TYPE, 1>(L, st);                          \
+      case 2: return tti_r_##SUFFIX<TYPE, 2>(L, st);                          \
+      case 3: return tti_r_##SUFFIX<TYPE, 3>(L, st);                          \
+      case 4: return tti_r_##SUFFIX<TYPE, 4>(L, st);                          \
+      case 5: return tti_r_##SUFFIX<TYPE, 5>(L, st);                          \
+      case 6: return tti_r_##SUFFIX<TYPE, 6>(L, st);                          \
+      case 7: return tti_r_##SUFFIX<TYPE, 7>(L, st);                          \
+      case 8: return tti_r_##SUFFIX<TYPE, 8>(L, st);                          \
+      default: return cudaErrorInvalidValue;                                  \
+    }                                                                         \
+  }                                                                           \
+  int tti_geom_##SUFFIX(int r, int tile, TileGeom *g) {                       \
     switch (r) {                                                              \
-      case 1: tti_geom_r<TYPE, 1>(g); return 0;                               \
-      case 2: tti_geom_r<TYPE, 2>(g); return 0;                               \
-      case 3: tti_geom_r<TYPE, 3>(g); return 0;                               \
-      case 4: tti_geom_r<TYPE, 4>(g); return 0;                               \
-      case 5: tti_geom_r<TYPE, 5>(g); return 0;                               \
-      case 6: tti_geom_r<TYPE, 6>(g); return 0;                               \
-      case 7: tti_geom_r<TYPE, 7>(g); return 0;                               \
-      case 8: tti_geom_r<TYPE, 8>(g); return 0;                               \
+      case 1: return tti_geom_r_##SUFFIX<TYPE, 1>(tile, g);                   \
+      case 2: return tti_geom_r_##SUFFIX<TYPE, 2>(tile, g);                   \
+      case 3: return tti_geom_r_##SUFFIX<TYPE, 3>(tile, g);                   \
+      case 4: return tti_geom_r_##SUFFIX<TYPE, 4>(tile, g);                   \
+      case 5: return tti_geom_r_##SUFFIX<TYPE, 5>(tile, g);                   \
+      case 6: return tti_geom_r_##SUFFIX<TYPE, 6>(tile, g);                   \
+      case 7: return tti_geom_r_##SUFFIX<TYPE, 7>(tile, g);                   \
+      case 8: return tti_geom_r_##SUFFIX<TYPE, 8>(tile, g);                   \
       default: return -1;                                                     \
     }                                                                         \
   }
