@@ -353,6 +353,14 @@ long long fdw_closure_num_params(void);
 int fdw_closure_create(fdw_closure **out, void *stream);
 int fdw_closure_destroy(fdw_closure *c);
 
+/*
+ * Inference kernels of fdw_step_closure: 0 (default) = one fused kernel on
+ * the tensor cores (mma.sync, FP16 operands: the BF16 weights exactly, the
+ * activations rounded to FP16; FP32 accumulation), 1 = plain FP32
+ * convolutions on the CUDA cores (the cross-check). Errors: INVALID_ARG.
+ */
+int fdw_closure_set_variant(fdw_closure *c, int variant);
+
 /* Set (resets the Adam state) / read the FP32 parameters (host or device). */
 int fdw_closure_set_params(fdw_closure *c, const float *params, int ptr_is_device);
 int fdw_closure_get_params(fdw_closure *c, float *params, int ptr_is_device);

@@ -407,22 +407,35 @@ cudaError_t closure_forward_batch(const float *x, const __nv_bfloat16 *pb, const
   return cudaGetLastError();
 }
 
+// Inference workspace for one grid: the FP32 path keeps the inputs and both
+// hidden layers on the whole grid (35 floats per point), the tensor-core
+// path only its FP16 inputs and the network output (closure_tc.cu); both
+// keep net(x0) and the normalisation.
 int closure_reserve_infer(ClosureNet *c, Dims d) {
   const size_t vol = (size_t)d.NX * d.NY * d.NZ;
-  if (c->infer_cap >= vol) return 0;
-  cudaFree(c->x); cudaFree(c->ia1); cudaFree(c->ia2); cudaFree(c->base);
-  c->x = c->ia1 = c->ia2 = c->base = nullptr;
-  c->infer_cap = 0;
-  if (cudaMalloc(&c->x, 3 * vol * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&c->base, vol * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&c->ia1, (size_t)kH * vol * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&c->ia2, (size_t)kH * vol * sizeof(float)) != cudaSuccess) {
-    cudaGetLastError();
-    return -1;
+  if (c->infer_cap < vol) {
+    cudaFree(c->x); cudaFree(c->ia1); cudaFree(c->ia2); cudaFree(c->base);
+    c->x = c->ia1 = c->ia2 = c->base = nullptr;
+    c->infer_cap = 0;
+    if (cudaMalloc(&c->base, vol * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    c->infer_cap = vol;
   }
   if (!c->s_dev && cudaMalloc(&c->s_dev, sizeof(float)) != cudaSuccess) return -1;
   if (!c->s_partial && cudaMalloc(&c->s_partial, 1024 * sizeof(float)) != cudaSuccess) return -1;
-  c->infer_cap = vol;
+  if (c->variant == 0) return closure_tc_reserve(c, d);
+  if (!c->x) {
+    if (cudaMalloc(&c->x, 3 * vol * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c->ia1, (size_t)kH * vol * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c->ia2, (size_t)kH * vol * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(c->x); cudaFree(c->ia1); cudaFree(c->ia2);
+      c->x = c->ia1 = c->ia2 = nullptr;
+      return -1;
+    }
+  }
   return 0;
 }
 
@@ -441,6 +454,7 @@ static cudaError_t infer_pre_t(ClosureNet *c, const T *u, const T *um, const flo
 
 cudaError_t closure_infer_base(ClosureNet *c, const float *vp, int nx, int ny, int nz, int nb, Dims d,
                                cudaStream_t st) {
+  if (c->variant == 0) return closure_tc_base(c, vp, nx, ny, nz, nb, d, st);
   const long long vol = (long long)d.NX * d.NY * d.NZ;
   closure_inputs_kernel<float><<<grid_for(vol), 256, 0, st>>>(nullptr, nullptr, vp, nx, ny, nz, nb, d, c->s_dev,
                                                               c->x);
@@ -451,8 +465,25 @@ cudaError_t closure_infer_base(ClosureNet *c, const float *vp, int nx, int ny, i
   return cudaGetLastError();
 }
 
+template <typename T>
+static void absmax_t(ClosureNet *c, const T *u, Dims d, cudaStream_t st) {
+  absmax_partial_kernel<T><<<1024, 256, 0, st>>>(u, d, c->s_partial);
+  absmax_final_kernel<<<1, 256, 0, st>>>(c->s_partial, 1024, c->s_dev);
+}
+
 cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const void *um, const float *vp,
                               int nx, int ny, int nz, int nb, Dims d, cudaStream_t st) {
+  if (c->variant == 0) {
+    switch (storage) {
+      case FDW_F32: absmax_t(c, (const float *)u, d, st); break;
+      case FDW_BF16: absmax_t(c, (const __nv_bfloat16 *)u, d, st); break;
+      case FDW_F16: absmax_t(c, (const __half *)u, d, st); break;
+      default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return closure_tc_net(c, storage, u, um, vp, nx, ny, nz, nb, d, st);
+  }
   switch (storage) {
     case FDW_F32: return infer_pre_t<float>(c, (const float *)u, (const float *)um, vp, nx, ny, nz, nb, d, st);
     case FDW_BF16:
@@ -463,9 +494,48 @@ cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const v
   }
 }
 
+// Tensor-core path: u_{n+1} += s * (net(x) - net(x0)) from the network
+// output, on the points whose receptive field is physical.
+template <typename T>
+__global__ void closure_apply_out_kernel(const float *__restrict__ net, const float *__restrict__ base,
+                                         const float *__restrict__ s_dev, T *__restrict__ u, Dims d, int nb,
+                                         int nx, int ny, int nz) {
+  const float s = *s_dev;
+  const long long vol = (long long)d.NX * d.NY * d.NZ;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < vol;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(q % d.NX);
+    const long long r = q / d.NX;
+    const int y = (int)(r % d.NY), z = (int)(r / d.NY);
+    if (x < nb + kHalo || x >= nb + nx - kHalo || y < nb + kHalo || y >= nb + ny - kHalo ||
+        z < nb + kHalo || z >= nb + nz - kHalo)
+      continue;
+    const size_t pp = ((size_t)z * d.NY + y) * d.Xp + x;
+    u[pp] = St<T>::st(St<T>::ld(u[pp]) + s * (net[q] - base[q]));
+  }
+}
+
 cudaError_t closure_infer_apply(ClosureNet *c, int storage, void *unew, Dims d, int nx, int ny, int nz, int nb,
                                 cudaStream_t st) {
   const long long vol = (long long)d.NX * d.NY * d.NZ;
+  if (c->variant == 0) {
+    switch (storage) {
+      case FDW_F32:
+        closure_apply_out_kernel<float><<<grid_for(vol), 256, 0, st>>>(c->tc_out, c->base, c->s_dev, (float *)unew,
+                                                                       d, nb, nx, ny, nz);
+        break;
+      case FDW_BF16:
+        closure_apply_out_kernel<__nv_bfloat16><<<grid_for(vol), 256, 0, st>>>(
+            c->tc_out, c->base, c->s_dev, (__nv_bfloat16 *)unew, d, nb, nx, ny, nz);
+        break;
+      case FDW_F16:
+        closure_apply_out_kernel<__half><<<grid_for(vol), 256, 0, st>>>(c->tc_out, c->base, c->s_dev,
+                                                                        (__half *)unew, d, nb, nx, ny, nz);
+        break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   switch (storage) {
     case FDW_F32:
       closure_apply_kernel<float><<<grid_for(vol), 256, 0, st>>>(c->ia2, c->pb + kOffW3, c->pf + kOffB3, c->base, c->s_dev,
@@ -605,7 +675,14 @@ extern "C" int fdw_closure_destroy(fdw_closure *c) {
   cudaFree(c->partial); cudaFree(c->loss_partial);
   cudaFree(c->xpair);
   cudaFree(c->x); cudaFree(c->ia1); cudaFree(c->ia2); cudaFree(c->base); cudaFree(c->s_dev); cudaFree(c->s_partial);
+  cudaFree(c->x16); cudaFree(c->tc_out); cudaFree(c->tcw);
   delete c;
+  return FDW_OK;
+}
+
+extern "C" int fdw_closure_set_variant(fdw_closure *c, int variant) {
+  if (!c || variant < 0 || variant > 1) return report_error(FDW_ERR_INVALID_ARG, "variant must be 0 or 1");
+  c->variant = variant;
   return FDW_OK;
 }
 

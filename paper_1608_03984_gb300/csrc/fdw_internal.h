@@ -186,6 +186,11 @@ struct ClosureNet {
   size_t xcap = 0;                // floats in xpair
   // inference workspace (one computational grid); base = net(0, 0, v)
   float *x = nullptr, *ia1 = nullptr, *ia2 = nullptr, *base = nullptr, *s_dev = nullptr;
+  // tensor-core inference (closure_tc.cu): FP16 inputs, network output, weights
+  void *x16 = nullptr, *tcw = nullptr;
+  float *tc_out = nullptr;
+  size_t tc_cap = 0;
+  int variant = 0;                // 0: tensor-core kernel, 1: FP32 CUDA-core kernels
   float *s_partial = nullptr;     // per-block maxima of |u_n|
   size_t infer_cap = 0;           // points
 };
@@ -201,6 +206,12 @@ cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const v
 cudaError_t closure_infer_apply(ClosureNet *c, int storage, void *unew, Dims d, int nx, int ny, int nz, int nb,
                                 cudaStream_t st);
 int closure_reserve_infer(ClosureNet *c, Dims d);
+// tensor-core path (closure_tc.cu)
+int closure_tc_reserve(ClosureNet *c, Dims d);
+cudaError_t closure_tc_base(ClosureNet *c, const float *vp, int nx, int ny, int nz, int nb, Dims d,
+                            cudaStream_t st);
+cudaError_t closure_tc_net(ClosureNet *c, int storage, const void *u, const void *um, const float *vp, int nx,
+                           int ny, int nz, int nb, Dims d, cudaStream_t st);
 
 }  // namespace fdw
 

@@ -70,6 +70,7 @@ _SIGS = {
     "fdw_closure_num_params": ([], ctypes.c_longlong),
     "fdw_closure_create": ([ctypes.POINTER(_P), _P], _I),
     "fdw_closure_destroy": ([_P], _I),
+    "fdw_closure_set_variant": ([_P, _I], _I),
     "fdw_closure_set_params": ([_P, _P, _I], _I),
     "fdw_closure_get_params": ([_P, _P, _I], _I),
     "fdw_closure_forward": ([_P, _P, _I, _I, _P], _I),
@@ -203,6 +204,11 @@ class Closure:
             self.close()
         except Exception:
             pass
+
+    def set_variant(self, variant):
+        """Inference kernels of Solver.step_closure: 0 tensor cores (default),
+        1 FP32 CUDA-core convolutions."""
+        _chk(lib().fdw_closure_set_variant(self._h, int(variant)))
 
     def set_params(self, p):
         ptr, dev, keep = _ptr(p, np.float32)

@@ -176,12 +176,13 @@ def _coarse_case(fdw, O, seed, storage="f32"):
 
 
 def test_step_closure_matches_oracle(fdw, O):
-    """Five coarse steps with the closure (order 4, 22 x 24 x 26 physical,
-    sponge 5, a point source, random initial levels) against the oracle's
-    closure step on the same BF16-rounded weights."""
+    """Five coarse steps with the closure's FP32 inference kernels (order 4,
+    22 x 24 x 26 physical, sponge 5, a point source, random initial levels)
+    against the oracle's closure step on the same BF16-rounded weights."""
     solver, setup, vp, src, wav, u0, um = _coarse_case(fdw, O, 31)
     p = random_params(7, scale=0.3)
     net = fdw.Closure()
+    net.set_variant(1)  # FP32 inference kernels
     net.set_params(p)
     ref_u, ref_um = u0.astype(np.float64), um.astype(np.float64)
     for k in range(5):
@@ -221,6 +222,7 @@ def test_step_closure_16bit_storage(fdw, O, storage):
     solver, setup, vp, src, wav, u0, um = _coarse_case(fdw, O, 51, storage)
     p = random_params(8, scale=0.3)
     net = fdw.Closure()
+    net.set_variant(1)
     net.set_params(p)
     ref_u, ref_um = solver.wavefield(0, 0).astype(np.float64), solver.wavefield(0, 1).astype(np.float64)
     for k in range(3):
@@ -231,6 +233,89 @@ def test_step_closure_16bit_storage(fdw, O, storage):
     assert rel(solver.wavefield(0, 0), ref_u) < tol
     net.close()
     solver.close()
+
+
+def _tc_vs_oracle_correction(fdw, O, seed, pscale):
+    """(GPU correction, oracle correction) of one closure step from random
+    levels: the closure step's u_{n+1} minus the plain step's (the source
+    term cancels)."""
+    solver, setup, vp, src, wav, u0, um = _coarse_case(fdw, O, seed)
+    plain, *_ = _coarse_case(fdw, O, seed)
+    p = random_params(seed, scale=pscale)
+    net = fdw.Closure()
+    net.set_params(p)
+    solver.step_closure(net, 1)
+    plain.step(1)
+    got = solver.wavefield(0, 0).astype(np.float64) - plain.wavefield(0, 0).astype(np.float64)
+    u, v = u0.astype(np.float64), um.astype(np.float64)
+    ref = O.closure_step(setup, u, v, vp, p.astype(np.float64)) - O.acoustic_step(setup, u, v)
+    net.close()
+    solver.close()
+    plain.close()
+    return got, ref
+
+
+@pytest.mark.parametrize("seed", [61, 62])
+def test_tensor_core_step_matches_oracle(fdw, O, seed):
+    """The fused tensor-core inference (FP16 operands, FP32 accumulation)
+    against the oracle's FP64 closure step: the correction agrees to the
+    FP16 rounding of the activations. Bound: each activation carries a
+    relative rounding error <= 2^-11; through two layers of 432-term sums
+    the correction's relative L2 error stays well below 1e-2."""
+    got, ref = _tc_vs_oracle_correction(fdw, O, seed, 0.3)
+    assert np.linalg.norm(ref) > 0
+    assert rel(got, ref) < 1e-2
+
+
+def test_tensor_core_matches_fp32_kernels(fdw, O):
+    """Tensor-core and FP32 inference kernels on the same state: the
+    corrections agree to FP16 rounding (the grid, 32 x 34 x 36 with the
+    sponge, is ragged for the 30 x 14 tile and split in two z chunks)."""
+    corr = []
+    for variant in (0, 1):
+        solver, *_ = _coarse_case(fdw, O, 71)
+        plain, *_ = _coarse_case(fdw, O, 71)
+        net = fdw.Closure()
+        net.set_variant(variant)
+        net.set_params(random_params(71, scale=0.3))
+        solver.step_closure(net, 1)
+        plain.step(1)
+        corr.append(solver.wavefield(0, 0).astype(np.float64) - plain.wavefield(0, 0))
+        net.close()
+        solver.close()
+        plain.close()
+    assert rel(corr[0], corr[1]) < 1e-2
+
+
+def test_tensor_core_correction_is_exactly_zero_where_the_field_is(fdw):
+    """net(x) - net(x0) is computed by the same deterministic kernel for x
+    and x0, so a wavefield that is zero over a point's receptive field gets
+    no correction at all: a blob in one corner leaves the far corner exactly
+    zero after a closure step, and a zero field stays exactly zero."""
+    from paper_1608_03984_gb300 import synth
+    n, nb, h = 40, 6, 20.0
+    vp = synth.random_velocity((n, n, n), h, 120.0, 81)
+    s = fdw.Solver(vp.shape, h, nb, 4)
+    s.set_model(vp).set_sponge(4500.0).set_dt(0.35 * h / 4500.0)
+    comp = s.comp_shape
+    u = np.zeros(comp, np.float32)
+    u[8:14, 8:14, 8:14] = synth.random_wavefield((6, 6, 6), 82)
+    s.set_wavefield(u, 0, 0)
+    s.set_wavefield(u, 0, 1)
+    net = fdw.Closure()
+    net.set_params(random_params(83, scale=0.3))
+    s.step_closure(net, 1)
+    out = s.wavefield(0, 0)
+    assert np.abs(out[8:14, 8:14, 8:14]).max() > 0
+    # beyond the blob + stencil radius 2 + receptive field 3 nothing moved
+    assert np.all(out[20:, 20:, 20:] == 0)
+    z = fdw.Solver(vp.shape, h, nb, 4)
+    z.set_model(vp).set_sponge(4500.0).set_dt(0.35 * h / 4500.0)
+    z.step_closure(net, 3)
+    assert np.all(z.wavefield(0, 0) == 0) and np.all(z.wavefield(0, 1) == 0)
+    net.close()
+    s.close()
+    z.close()
 
 
 def test_training_reduces_error_on_held_out_models(fdw):
