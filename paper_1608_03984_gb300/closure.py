@@ -302,12 +302,13 @@ def unexplained(net: "fdwave.Closure", sampler, count=512, seed=1):
 
 
 def receivers(pr: Pairing, nside=8):
-    """A nside x nside grid of receivers at 2 coarse spacings depth, on
+    """A nside x nside grid of receivers at 5 coarse spacings depth (below
+    the 3-point band next to the sponge that the closure leaves alone), on
     points of both grids."""
     span = (pr.n_c - 1) * pr.h_c
     g = np.round(np.linspace(0.1 * span, 0.9 * span, nside) / pr.h_c) * pr.h_c
     X, Y = np.meshgrid(g, g)
-    return np.stack([X.ravel(), Y.ravel(), np.full(X.size, 2 * pr.h_c)], axis=1)
+    return np.stack([X.ravel(), Y.ravel(), np.full(X.size, 5 * pr.h_c)], axis=1)
 
 
 def evaluate(pr: Pairing, net, seed: int, nt_c: int, timing=False, closure_from=None):

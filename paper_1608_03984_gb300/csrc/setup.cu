@@ -9,26 +9,27 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 
 // Medium extension into the sponge: a computational point takes the value
 // of the nearest physical point.
-__device__ __forceinline__ size_t phys_index(int i, int j, int k, int nx, int ny, int nz, int nb) {
-  const int pi = clampi(i - nb, 0, nx - 1), pj = clampi(j - nb, 0, ny - 1), pk = clampi(k - nb, 0, nz - 1);
-  return ((size_t)pk * ny + pj) * nx + pi;
-}
 
+// The field kernels walk rows: a block takes rows (j, k) of the padded
+// layout in turn and its threads the x points of a row, so the index
+// arithmetic is one division per row (64-bit division per element made
+// these kernels issue-bound at a fraction of the HBM bandwidth).
 template <typename T>
 __global__ void coef_acoustic_kernel(const float *__restrict__ vp, int nx, int ny, int nz, int nb,
                                      Dims d, double dt_over_h, T *__restrict__ c) {
-  const size_t n = d.vol();
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
-       p += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(p % d.Xp);
-    const size_t rest = p / d.Xp;
-    const int j = (int)(rest % d.NY), k = (int)(rest / d.NY);
-    float v = 0.f;
-    if (i < d.NX) {
-      const double cv = (double)vp[phys_index(i, j, k, nx, ny, nz, nb)] * dt_over_h;
-      v = (float)(cv * cv);
+  const int rows = d.NY * d.NZ;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % d.NY, k = row / d.NY;
+    T *cr = c + (size_t)row * d.Xp;
+    const float *vr = vp + ((size_t)clampi(k - nb, 0, nz - 1) * ny + clampi(j - nb, 0, ny - 1)) * nx;
+    for (int i = threadIdx.x; i < d.Xp; i += blockDim.x) {
+      float v = 0.f;
+      if (i < d.NX) {
+        const double cv = (double)vr[clampi(i - nb, 0, nx - 1)] * dt_over_h;
+        v = (float)(cv * cv);
+      }
+      cr[i] = St<T>::st(v);
     }
-    c[p] = St<T>::st(v);
   }
 }
 
@@ -37,36 +38,34 @@ __global__ void coef_tti_kernel(const float *__restrict__ vp, const float *__res
                                 const float *__restrict__ delta, const float *__restrict__ theta,
                                 const float *__restrict__ phi, int nx, int ny, int nz, int nb,
                                 Dims d, double dt_over_h, T *c, T *e, T *dl, T *ax, T *ay) {
-  const size_t n = d.vol();
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
-       p += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(p % d.Xp);
-    const size_t rest = p / d.Xp;
-    const int j = (int)(rest % d.NY), k = (int)(rest / d.NY);
-    float vc = 0.f, ve = 0.f, vd = 0.f, vx = 0.f, vy = 0.f;
-    if (i < d.NX) {
-      const size_t q = phys_index(i, j, k, nx, ny, nz, nb);
-      const double cv = (double)vp[q] * dt_over_h;
-      vc = (float)(cv * cv);
-      ve = (float)(1.0 + 2.0 * (double)eps[q]);
-      vd = (float)sqrt(1.0 + 2.0 * (double)delta[q]);
-      const double th = theta[q], ph = phi[q];
-      double sx = sin(th) * cos(ph), sy = sin(th) * sin(ph);
-      if (cos(th) < 0.0) { sx = -sx; sy = -sy; }  // n and -n give the same operator
-      vx = (float)sx;
-      vy = (float)sy;
+  const int rows = d.NY * d.NZ;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % d.NY, k = row / d.NY;
+    const size_t pr = ((size_t)clampi(k - nb, 0, nz - 1) * ny + clampi(j - nb, 0, ny - 1)) * nx;
+    for (int i = threadIdx.x; i < d.Xp; i += blockDim.x) {
+      const size_t p = (size_t)row * d.Xp + i;
+      float vc = 0.f, ve = 0.f, vd = 0.f, vx = 0.f, vy = 0.f;
+      if (i < d.NX) {
+        const size_t q = pr + clampi(i - nb, 0, nx - 1);
+        const double cv = (double)vp[q] * dt_over_h;
+        vc = (float)(cv * cv);
+        ve = (float)(1.0 + 2.0 * (double)eps[q]);
+        vd = (float)sqrt(1.0 + 2.0 * (double)delta[q]);
+        const double th = theta[q], ph = phi[q];
+        double sx = sin(th) * cos(ph), sy = sin(th) * sin(ph);
+        if (cos(th) < 0.0) { sx = -sx; sy = -sy; }  // n and -n give the same operator
+        vx = (float)sx;
+        vy = (float)sy;
+      }
+      c[p] = St<T>::st(vc);
+      e[p] = St<T>::st(ve);
+      dl[p] = St<T>::st(vd);
+      ax[p] = St<T>::st(vx);
+      ay[p] = St<T>::st(vy);
     }
-    c[p] = St<T>::st(vc);
-    e[p] = St<T>::st(ve);
-    dl[p] = St<T>::st(vd);
-    ax[p] = St<T>::st(vx);
-    ay[p] = St<T>::st(vy);
   }
 }
 
-// out[0] = max vp, out[1] = max vp sqrt(1 + 2 eps) (eps may be null), as
-// float bits (positive floats order like their bit patterns); out[2] = 1 if
-// some vp is not a positive finite number.
 __global__ void max_velocity_kernel(const float *__restrict__ vp, const float *__restrict__ eps,
                                     long n, float *out) {
   float m0 = 0.f, m1 = 0.f;
@@ -91,34 +90,33 @@ __global__ void max_velocity_kernel(const float *__restrict__ vp, const float *_
 
 template <typename T>
 __global__ void pack_kernel(const float *__restrict__ src, T *__restrict__ dst, Dims d, float scale) {
-  const size_t n = d.vol();
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
-       p += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(p % d.Xp);
-    const size_t row = p / d.Xp;
-    dst[p] = St<T>::st(i < d.NX ? scale * src[row * d.NX + i] : 0.f);
-  }
+  const int rows = d.NY * d.NZ;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int i = threadIdx.x; i < d.Xp; i += blockDim.x)
+      dst[(size_t)row * d.Xp + i] = St<T>::st(i < d.NX ? scale * src[(size_t)row * d.NX + i] : 0.f);
 }
 
 template <typename T>
 __global__ void unpack_kernel(const T *__restrict__ src, float *__restrict__ dst, Dims d, float scale) {
-  const size_t n = (size_t)d.NX * d.NY * d.NZ;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
-       p += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(p % d.NX);
-    const size_t row = p / d.NX;
-    dst[p] = scale * St<T>::ld(src[row * d.Xp + i]);
-  }
+  const int rows = d.NY * d.NZ;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int i = threadIdx.x; i < d.NX; i += blockDim.x)
+      dst[(size_t)row * d.NX + i] = scale * St<T>::ld(src[(size_t)row * d.Xp + i]);
 }
 
 template <typename T>
 __global__ void nonfinite_kernel(const T *__restrict__ f, Dims d, int *flag) {
-  const size_t n = d.vol();
+  const int rows = d.NY * d.NZ;
   int bad = 0;
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
-       p += (size_t)gridDim.x * blockDim.x)
-    bad |= !isfinite(St<T>::ld(f[p]));
+  for (int row = blockIdx.x; row < rows; row += gridDim.x)
+    for (int i = threadIdx.x; i < d.Xp; i += blockDim.x) bad |= !isfinite(St<T>::ld(f[(size_t)row * d.Xp + i]));
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// one block per row (rows of a computational grid; capped)
+static int row_grid(const Dims &d) {
+  const long r = (long)d.NY * d.NZ;
+  return (int)(r < 152 * 64 ? (r < 1 ? 1 : r) : 152 * 64);
 }
 
 static int grid_for(size_t n) {
@@ -136,7 +134,7 @@ static int grid_for(size_t n) {
 
 cudaError_t launch_coef_acoustic(int storage, const float *vp, int nx, int ny, int nz, int nb,
                                  Dims d, double dt_over_h, void *c, cudaStream_t st) {
-  FDW_DISPATCH(storage, (coef_acoustic_kernel<T><<<grid_for(d.vol()), 256, 0, st>>>(
+  FDW_DISPATCH(storage, (coef_acoustic_kernel<T><<<row_grid(d), 256, 0, st>>>(
                             vp, nx, ny, nz, nb, d, dt_over_h, (T *)c)));
   return cudaGetLastError();
 }
@@ -145,7 +143,7 @@ cudaError_t launch_coef_tti(int storage, const float *vp, const float *eps, cons
                             const float *theta, const float *phi, int nx, int ny, int nz, int nb,
                             Dims d, double dt_over_h, void *c, void *e, void *dl, void *ax,
                             void *ay, cudaStream_t st) {
-  FDW_DISPATCH(storage, (coef_tti_kernel<T><<<grid_for(d.vol()), 256, 0, st>>>(
+  FDW_DISPATCH(storage, (coef_tti_kernel<T><<<row_grid(d), 256, 0, st>>>(
                             vp, eps, delta, theta, phi, nx, ny, nz, nb, d, dt_over_h, (T *)c,
                             (T *)e, (T *)dl, (T *)ax, (T *)ay)));
   return cudaGetLastError();
@@ -161,19 +159,19 @@ cudaError_t launch_max_velocity(const float *vp, const float *eps, long n, float
 
 cudaError_t launch_pack(int storage, const float *src, void *dst, Dims d, float scale,
                         cudaStream_t st) {
-  FDW_DISPATCH(storage, (pack_kernel<T><<<grid_for(d.vol()), 256, 0, st>>>(src, (T *)dst, d, scale)));
+  FDW_DISPATCH(storage, (pack_kernel<T><<<row_grid(d), 256, 0, st>>>(src, (T *)dst, d, scale)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_unpack(int storage, const void *src, Dims d, float *dst, float scale,
                           cudaStream_t st) {
-  FDW_DISPATCH(storage, (unpack_kernel<T><<<grid_for((size_t)d.NX * d.NY * d.NZ), 256, 0, st>>>(
+  FDW_DISPATCH(storage, (unpack_kernel<T><<<row_grid(d), 256, 0, st>>>(
                             (const T *)src, dst, d, scale)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_nonfinite(int storage, const void *f, Dims d, int *flag, cudaStream_t st) {
-  FDW_DISPATCH(storage, (nonfinite_kernel<T><<<grid_for(d.vol()), 256, 0, st>>>(
+  FDW_DISPATCH(storage, (nonfinite_kernel<T><<<row_grid(d), 256, 0, st>>>(
                             (const T *)f, d, flag)));
   return cudaGetLastError();
 }
