@@ -88,6 +88,21 @@ cudaError_t acoustic_prepare(int storage, int r, int tile) {
   return launch_acoustic(L, 0);
 }
 
+int acoustic_ctas_per_sm(int storage, int r, int tile) {
+  int occ = 0;
+  AcousticLaunch L{};
+  L.storage = storage;
+  L.r = r;
+  L.tile = tile;
+  L.prepare_only = 1;
+  L.occupancy_out = &occ;
+  if (launch_acoustic(L, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
+}
+
 int acoustic_geom(int storage, int r, int tile, TileGeom *g) {
   switch (storage) {
     case FDW_F32: return acoustic_geom_f32(r, tile, g);

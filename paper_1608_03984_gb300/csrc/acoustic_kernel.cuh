@@ -268,8 +268,12 @@ template <typename T, int R, int RX, int RY, int BY, int NS, int U>
 cudaError_t launch_acoustic_cfg(const AcousticLaunch &L, cudaStream_t st) {
   using C = AcTile<T, R, RX, RY, BY, NS, U>;
   auto kern = acoustic_tma_kernel<T, R, RX, RY, BY, NS, U>;
-  if (L.prepare_only)
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_B);
+  if (L.prepare_only) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_B);
+    if (e == cudaSuccess && L.occupancy_out)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(L.occupancy_out, kern, C::THREADS, C::SMEM_B);
+    return e;
+  }
   const int zch = L.zchunks < 1 ? 1 : L.zchunks;
   const int zc = (L.d.NZ + zch - 1) / zch;
   if (zc > kMaxZChunk) return cudaErrorInvalidValue;

@@ -254,23 +254,54 @@ void drop_graphs(fdw_solver *s) {
 // shared memory).
 int min_zchunks(const fdw_solver *s) { return (s->d.NZ + kMaxZChunk - 1) / kMaxZChunk; }
 
+// Default number of z chunks of the 2.5D kernels (measured on the 592^3
+// acoustic and 464^3 TTI workloads).
+// FP32 acoustic kernel: a CTA marching a chunk of L planes does L + 2r
+// plane iterations (the queue fill) and the grid runs in waves of (SMs x
+// resident CTAs per SM); the time is modelled as
+//   ceil(CTAs / slots) x (ceil(NZ / chunks) + 2r)
+// and minimised over the chunk counts that keep at least max(16, 4r)
+// planes per chunk: this picks the measured best chunking at every order.
+// The TTI kernel and the 16-bit acoustic kernels (more resident CTAs, short
+// fills) run best with more, smaller chunks: about 16 (TTI) or 32 (16-bit
+// acoustic) CTAs per SM in total.
 int default_zchunks(const fdw_solver *s) {
   TileGeom tg;
-  const int bad = s->eq == FDW_TTI ? tti_geom(s->storage, s->r, s->tile, &tg)
-                                   : acoustic_geom(s->storage, s->r, s->tile, &tg);
+  const bool tti = s->eq == FDW_TTI;
+  const int bad = tti ? tti_geom(s->storage, s->r, s->tile, &tg) : acoustic_geom(s->storage, s->r, s->tile, &tg);
   if (bad) return 1;
-  const int bix = tg.box_int_x, biy = tg.box_int_y;
-  const long tiles = (long)((s->d.NX + bix - 1) / bix) * ((s->d.NY + biy - 1) / biy);
-  // about 16 CTAs per SM in total (32 for the acoustic kernel with 16-bit
-  // storage, whose stages are half the size: measured +3-4% at 592^3)
-  const long per_sm = (s->eq == FDW_ACOUSTIC && s->storage != FDW_F32) ? 32 : 16;
-  long want = (152L * per_sm + tiles - 1) / tiles;
+  const long tiles = (long)((s->d.NX + tg.box_int_x - 1) / tg.box_int_x) * ((s->d.NY + tg.box_int_y - 1) / tg.box_int_y);
   const int zmin = 4 * s->r > 16 ? 4 * s->r : 16;
   long maxch = s->d.NZ / zmin;
   if (maxch < 1) maxch = 1;
-  if (want > maxch) want = maxch;
-  if (want < 1) want = 1;
-  return min_zchunks(s) > want ? min_zchunks(s) : (int)want;
+  const int lo = min_zchunks(s);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 152;
+  }
+  if (tti || s->storage != FDW_F32) {
+    const long per_sm = tti ? 16 : 32;
+    long want = ((long)sms * per_sm + tiles - 1) / tiles;
+    if (want > maxch) want = maxch;
+    if (want < 1) want = 1;
+    return lo > want ? lo : (int)want;
+  }
+  int occ = acoustic_ctas_per_sm(s->storage, s->r, s->tile);
+  if (occ < 1) occ = 1;
+  const long slots = (long)sms * occ;
+  long best = lo, best_cost = -1;
+  for (long ch = lo; ch <= (maxch > lo ? maxch : lo); ++ch) {
+    const long len = (s->d.NZ + ch - 1) / ch;
+    const long used = (s->d.NZ + len - 1) / len;  // chunks actually launched
+    const long waves = (tiles * used + slots - 1) / slots;
+    const long cost = waves * (len + 2 * s->r);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = ch;
+    }
+  }
+  return (int)best;
 }
 
 // Enqueue the stencil update of one time step from buffer `cur` on stream st.

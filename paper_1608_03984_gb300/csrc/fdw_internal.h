@@ -77,9 +77,13 @@ struct AcousticLaunch {
   int naive;              // 1 = one-thread-per-point kernel (debug cross-check)
   int prepare_only;       // 1 = only set kernel attributes (outside graph capture)
   int tile;               // tile configuration index of the 2.5D kernel
+  int *occupancy_out;     // with prepare_only: resident CTAs per SM of the configuration
 };
 cudaError_t launch_acoustic(const AcousticLaunch &L, cudaStream_t st);
 cudaError_t acoustic_prepare(int storage, int r, int tile);
+// Resident CTAs per SM of a configuration (sets its attributes); 0 on error.
+int acoustic_ctas_per_sm(int storage, int r, int tile);
+int tti_ctas_per_sm(int storage, int r, int tile);
 
 // Tile geometry of one configuration of the 2.5D acoustic kernel: the TMA
 // boxes (halo tile and interior tiles) the host encodes in tensor maps.
@@ -117,6 +121,7 @@ struct TTILaunch {
   int naive;
   int prepare_only;
   int tile;           // configuration index of the 2.5D kernel (tti_kernel.cuh)
+  int *occupancy_out; // with prepare_only: resident CTAs per SM of the configuration
   // tensor maps: halo tiles of p, r at level n; interior tiles of p, r at
   // level n-1 and of the medium fields
   const CUtensorMap *m_ph, *m_rh, *m_pm, *m_rm, *m_c, *m_e, *m_d, *m_ax, *m_ay;

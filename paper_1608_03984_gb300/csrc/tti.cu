@@ -134,6 +134,22 @@ int tti_default_tile(int storage, int r) {
   return r <= 4 ? 1 : r <= 6 ? 2 : 4;
 }
 
+int tti_ctas_per_sm(int storage, int r, int tile) {
+  int occ = 0;
+  TTILaunch L{};
+  memset(&L, 0, sizeof L);
+  L.storage = storage;
+  L.r = r;
+  L.tile = tile;
+  L.prepare_only = 1;
+  L.occupancy_out = &occ;
+  if (launch_tti(L, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return occ;
+}
+
 cudaError_t tti_prepare(int storage, int r, int tile) {
   TTILaunch L{};
   memset(&L, 0, sizeof L);
