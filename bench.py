@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--closure-models", type=int, default=10)
     p.add_argument("--closure-iters", type=int, default=8000)
     p.add_argument("--closure-eval", type=int, default=2, help="held-out models at full size")
+    p.add_argument("--profile-closure-step", type=int, default=0, metavar="N",
+                   help="only run 40 plain and 2 closure steps on an N^3 coarse grid (+20 sponge), "
+                        "random network: the case the closure kernel is profiled on")
     return p.parse_args()
 
 
@@ -622,8 +625,29 @@ def run_e2e(args, orders, base, stream):
                     "%d steps, traces read back; wall clock" % nsteps}
 
 
+def profile_closure_step(n):
+    """A small, fixed closure case for kernel profiling (not a measurement)."""
+    import torch
+    from paper_1608_03984_gb300 import closure as C, fdwave
+    torch.cuda.set_device(0)
+    pr = C.Pairing(n_c=n, nb_c=20, src_sigma=1.5)
+    v_f, v_c, src = C.model(pr, 5064)
+    cs = C.coarse_solver(pr, v_c, src, 100)
+    net = fdwave.Closure()
+    net.set_params(C.init_params(0, last_scale=0.3))
+    cs.step(40)
+    cs.step_closure(net, 2)
+    torch.cuda.synchronize()
+    net.close()
+    cs.close()
+    print("closure step case done")
+
+
 def main():
     args = parse()
+    if args.profile_closure_step:
+        profile_closure_step(args.profile_closure_step)
+        return
     orders = tuple(int(x) for x in args.orders.split(","))
     if args.impl == "reference":
         run_reference(args, orders)

@@ -93,9 +93,11 @@ __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r
 __device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t &r0, uint32_t &r1) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(addr));
 }
-// D += A (16x16, FP16) * B (16x8, FP16), FP32 accumulators
+// D += A (16x16, FP16) * B (16x8, FP16), FP32 accumulators. Not volatile:
+// it only reads and writes registers, so the compiler may schedule it
+// after later (volatile) fragment loads and hide their latency.
 __device__ __forceinline__ void mma16816(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
       "{%8, %9}, {%0, %1, %2, %3};"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -295,18 +297,23 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
           uint32_t aw[3][4];
 #pragma unroll
           for (int b = 0; b < 3; ++b) load_a(W1s + (a * 3 + b) * 256, lane, aw[b]);
+          // row yi of the input plane as this lane's ldmatrix row address
+          auto row_addr = [&](int yi) {
+            return (xi & 1) ? s_u32(inp + IN_E_B + (yi * WIS + xi + 1) * 8) : s_u32(inp + (yi * WIS + xi) * 8);
+          };
+          uint32_t bc0, bc1;
+          ldsm_x2(row_addr(yb), bc0, bc1);
 #pragma unroll
-          for (int yy = 0; yy < RY + 2; ++yy) {
-            const int yi = yb + yy;  // input row = layer-1 row + b
-            const uint32_t addr = (xi & 1) ? s_u32(inp + IN_E_B + (yi * WIS + xi + 1) * 8)
-                                           : s_u32(inp + (yi * WIS + xi) * 8);
-            uint32_t b0, b1;
-            ldsm_x2(addr, b0, b1);
+          for (int yy = 0; yy < RY + 2; ++yy) {  // input row yb + yy = layer-1 row + b
+            uint32_t bn0 = 0u, bn1 = 0u;
+            if (yy + 1 < RY + 2) ldsm_x2(row_addr(yb + yy + 1), bn0, bn1);
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
               const int r = yy - b;
-              if (r >= 0 && r < RY) mma16816(acc[r], aw[b], b0, b1);
+              if (r >= 0 && r < RY) mma16816(acc[r], aw[b], bc0, bc1);
             }
+            bc0 = bn0;
+            bc1 = bn1;
           }
         }
         // epilogue: bias, ReLU, zero outside the grid, FP16 into the ring
@@ -350,16 +357,20 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
 #pragma unroll
             for (int b = 0; b < 3; ++b) load_a(W2s + ((a * 3 + b) * 3 + c) * 256, lane, aw[b]);
             const int x1 = sx * 8 + n + c;  // layer-1 column = layer-2 column + c
+            // B fragments one row ahead of the MMAs that use them
+            uint32_t bc0, bc1;
+            ldsm_x2(s_u32(a1p + act_off(yb * W1R + x1, hk)), bc0, bc1);
 #pragma unroll
             for (int yy = 0; yy < RY + 2; ++yy) {
-              const int y1 = yb + yy;  // layer-1 row = layer-2 row + b
-              uint32_t b0, b1;
-              ldsm_x2(s_u32(a1p + act_off(y1 * W1R + x1, hk)), b0, b1);
+              uint32_t bn0 = 0u, bn1 = 0u;
+              if (yy + 1 < RY + 2) ldsm_x2(s_u32(a1p + act_off((yb + yy + 1) * W1R + x1, hk)), bn0, bn1);
 #pragma unroll
               for (int b = 0; b < 3; ++b) {
-                const int r = yy - b;
-                if (r >= 0 && r < RY) mma16816(acc[r], aw[b], b0, b1);
+                const int r = yy - b;  // layer-1 row yb + yy = layer-2 row yb + r, plus b
+                if (r >= 0 && r < RY) mma16816(acc[r], aw[b], bc0, bc1);
               }
+              bc0 = bn0;
+              bc1 = bn1;
             }
           }
         }
