@@ -164,6 +164,24 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value, device="cpu"):
+    """Largest value over the ranks of the default process group (the
+    slowest rank's time); the value itself without a group (one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank, world, ms):
+    """Gpts/s of the whole job: every rank's points over the slowest rank's
+    time (weak scaling: each rank runs its own replica of the workload)."""
+    return points_per_rank * world / (ms / 1e3) / 1e9
+
+
 def workload(args, order, nt):
     from paper_1608_03984_gb300 import synth
     return synth.random_acoustic(n=args.n, nb=args.nb, order=order, nt=nt, nrec_side=256)
@@ -310,14 +328,8 @@ def run_fdwave(args, orders):
     zchs = {o: s.zchunks for o, s in zip(orders, solvers)}
     for s in solvers:
         s.check()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-
-    total_pts = points * len(orders) * args.steps * world
-    value = total_pts / (ms / 1e3) / 1e9
+    ms = max_over_ranks(ms, device="cuda")
+    value = whole_job_rate(points * len(orders) * args.steps, world, ms)
     hbm, peak_src = peaks()
     per_order = {}
     sum_bytes, sum_kms = 0.0, 0.0
@@ -618,8 +630,11 @@ def run_e2e(args, orders, base, stream):
         h2d += vp_h.numel() * 4 + w_h.numel() * 4 + base.src_xyz.nbytes + base.rec_xyz.nbytes
         d2h += tr.nbytes
         s.close()
+    world, _, _ = dist_setup()
+    total = max_over_ranks(total, device="cuda")  # the slowest rank's wall clock
     pts = base.points * len(orders) * nsteps
-    return {"value": pts / total / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": h2d // nsteps,
+    return {"value": whole_job_rate(pts, world, total * 1e3), "unit": "Gpts/s",
+            "h2d_bytes_per_step": h2d // nsteps,
             "d2h_bytes_per_step": d2h // nsteps,
             "note": "per order: model/sources/receivers uploaded from pinned host memory, "
                     "%d steps, traces read back; wall clock" % nsteps}
