@@ -10,26 +10,31 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 // Medium extension into the sponge: a computational point takes the value
 // of the nearest physical point.
 
+// c' = (v dt/h)^2 in FP32 arithmetic accurate to a few ulp: dt/h as an
+// unevaluated sum hi + lo of two floats, v (hi + lo) = p + e exactly enough
+// (fmaf gives the rounding error of v hi), then (p + e)^2 ~ p^2 + 2 p e with
+// one rounding. (Computing it in FP64 made this set-up kernel take 1.6 ms at
+// 592^3: FP64 runs at a small fraction of the FP32 rate on this part.)
+__device__ __forceinline__ float coef_of(float v, float hi, float lo) {
+  const float p = v * hi;
+  const float e = fmaf(v, hi, -p) + v * lo;
+  return fmaf(p, p, 2.f * p * e);
+}
+
 // The field kernels walk rows: a block takes rows (j, k) of the padded
 // layout in turn and its threads the x points of a row, so the index
-// arithmetic is one division per row (64-bit division per element made
-// these kernels issue-bound at a fraction of the HBM bandwidth).
+// arithmetic is one division per row.
 template <typename T>
 __global__ void coef_acoustic_kernel(const float *__restrict__ vp, int nx, int ny, int nz, int nb,
                                      Dims d, double dt_over_h, T *__restrict__ c) {
+  const float hi = (float)dt_over_h, lo = (float)(dt_over_h - (double)hi);
   const int rows = d.NY * d.NZ;
   for (int row = blockIdx.x; row < rows; row += gridDim.x) {
     const int j = row % d.NY, k = row / d.NY;
     T *cr = c + (size_t)row * d.Xp;
     const float *vr = vp + ((size_t)clampi(k - nb, 0, nz - 1) * ny + clampi(j - nb, 0, ny - 1)) * nx;
-    for (int i = threadIdx.x; i < d.Xp; i += blockDim.x) {
-      float v = 0.f;
-      if (i < d.NX) {
-        const double cv = (double)vr[clampi(i - nb, 0, nx - 1)] * dt_over_h;
-        v = (float)(cv * cv);
-      }
-      cr[i] = St<T>::st(v);
-    }
+    for (int i = threadIdx.x; i < d.Xp; i += blockDim.x)
+      cr[i] = St<T>::st(i < d.NX ? coef_of(vr[clampi(i - nb, 0, nx - 1)], hi, lo) : 0.f);
   }
 }
 
@@ -38,6 +43,7 @@ __global__ void coef_tti_kernel(const float *__restrict__ vp, const float *__res
                                 const float *__restrict__ delta, const float *__restrict__ theta,
                                 const float *__restrict__ phi, int nx, int ny, int nz, int nb,
                                 Dims d, double dt_over_h, T *c, T *e, T *dl, T *ax, T *ay) {
+  const float hi = (float)dt_over_h, lo = (float)(dt_over_h - (double)hi);
   const int rows = d.NY * d.NZ;
   for (int row = blockIdx.x; row < rows; row += gridDim.x) {
     const int j = row % d.NY, k = row / d.NY;
@@ -46,16 +52,18 @@ __global__ void coef_tti_kernel(const float *__restrict__ vp, const float *__res
       const size_t p = (size_t)row * d.Xp + i;
       float vc = 0.f, ve = 0.f, vd = 0.f, vx = 0.f, vy = 0.f;
       if (i < d.NX) {
+        // FP32 arithmetic (FP64 is slow here): each value within a few ulp
         const size_t q = pr + clampi(i - nb, 0, nx - 1);
-        const double cv = (double)vp[q] * dt_over_h;
-        vc = (float)(cv * cv);
-        ve = (float)(1.0 + 2.0 * (double)eps[q]);
-        vd = (float)sqrt(1.0 + 2.0 * (double)delta[q]);
-        const double th = theta[q], ph = phi[q];
-        double sx = sin(th) * cos(ph), sy = sin(th) * sin(ph);
-        if (cos(th) < 0.0) { sx = -sx; sy = -sy; }  // n and -n give the same operator
-        vx = (float)sx;
-        vy = (float)sy;
+        vc = coef_of(vp[q], hi, lo);
+        ve = fmaf(2.f, eps[q], 1.f);
+        vd = sqrtf(fmaf(2.f, delta[q], 1.f));
+        float st, ct, sp, cp;
+        sincosf(theta[q], &st, &ct);
+        sincosf(phi[q], &sp, &cp);
+        float sx = st * cp, sy = st * sp;
+        if (ct < 0.f) { sx = -sx; sy = -sy; }  // n and -n give the same operator
+        vx = sx;
+        vy = sy;
       }
       c[p] = St<T>::st(vc);
       e[p] = St<T>::st(ve);
@@ -104,12 +112,12 @@ __global__ void unpack_kernel(const T *__restrict__ src, float *__restrict__ dst
       dst[(size_t)row * d.NX + i] = scale * St<T>::ld(src[(size_t)row * d.Xp + i]);
 }
 
+// (padding columns hold zeros, so the whole padded volume is scanned flat)
 template <typename T>
-__global__ void nonfinite_kernel(const T *__restrict__ f, Dims d, int *flag) {
-  const int rows = d.NY * d.NZ;
+__global__ void nonfinite_kernel(const T *__restrict__ f, size_t n, int *flag) {
   int bad = 0;
-  for (int row = blockIdx.x; row < rows; row += gridDim.x)
-    for (int i = threadIdx.x; i < d.Xp; i += blockDim.x) bad |= !isfinite(St<T>::ld(f[(size_t)row * d.Xp + i]));
+  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(St<T>::ld(f[p]));
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
@@ -171,8 +179,8 @@ cudaError_t launch_unpack(int storage, const void *src, Dims d, float *dst, floa
 }
 
 cudaError_t launch_nonfinite(int storage, const void *f, Dims d, int *flag, cudaStream_t st) {
-  FDW_DISPATCH(storage, (nonfinite_kernel<T><<<row_grid(d), 256, 0, st>>>(
-                            (const T *)f, d, flag)));
+  FDW_DISPATCH(storage, (nonfinite_kernel<T><<<grid_for(d.vol()), 256, 0, st>>>(
+                            (const T *)f, d.vol(), flag)));
   return cudaGetLastError();
 }
 
