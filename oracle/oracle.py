@@ -328,6 +328,37 @@ def acoustic_update_at(u_block, um_c, v_c, gamma_c, h, order, dt):
     return acoustic_step(s, u_block, um)[r, r, r]
 
 
+class _TtiBlockSetup(_BlockSetup):
+    """Medium of a small TTI block: every field constant (the centre's)."""
+
+    def __init__(self, shape, h, order, dt, v, eps, delta, theta, phi, gamma):
+        n = shape[0]
+        super().__init__(shape, h, 0, order, dt, dt * dt * float(v) ** 2, np.full(n, float(gamma)),
+                         np.zeros(n), np.zeros(n))
+        self.eps = np.full(shape, float(eps))
+        self.delta = np.full(shape, float(delta))
+        self.theta = np.full(shape, float(theta))
+        self.phi = np.full(shape, float(phi))
+
+
+def tti_update_at(p_block, pm_c, r_block, rm_c, v_c, eps_c, delta_c, theta_c, phi_c, gamma_c, h,
+                  order, dt):
+    """(p_{n+1}, r_{n+1}) at the centre of (2r+1)^3 blocks of p_n, r_n (no
+    source): the oracle's TTI step run on the blocks with the centre's medium
+    everywhere. The centre's operator reads p and r within r points along
+    each axis (second derivatives, and cross derivatives with both offsets
+    <= r) and the medium at the centre only, so it stays inside the block."""
+    r = order // 2
+    n = 2 * r + 1
+    assert p_block.shape == (n, n, n) and r_block.shape == (n, n, n)
+    s = _TtiBlockSetup((n, n, n), h, order, dt, v_c, eps_c, delta_c, theta_c, phi_c, gamma_c)
+    pm = np.zeros((n, n, n))
+    rm = np.zeros((n, n, n))
+    pm[r, r, r], rm[r, r, r] = pm_c, rm_c
+    pp, rp = tti_step(s, p_block, pm, r_block, rm)
+    return pp[r, r, r], rp[r, r, r]
+
+
 def extend_adjoint(g, nb):
     """Adjoint of `extend`: each physical point collects the computational
     points that copy its value (separable: per axis, the nb sponge slices

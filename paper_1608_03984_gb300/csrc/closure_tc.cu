@@ -9,9 +9,9 @@
 //   layer 2     : the current plane of a2 (FP16),
 //   layer 3     : per-tap products of the current a2 plane (FP32), gathered
 //                 into three pending output planes (FP32).
-// Three barriers per plane: layer 1 | layer 2 and the layer-3 products of
-// each warp's own layer-2 tile | gather, output and the next input plane
-// (prefetched into registers one plane ahead).
+// Two barriers per plane: [layer-3 gather of the previous plane + layer 1]
+// | [layer 2 and the layer-3 products of each warp's own layer-2 tile + the
+// next input plane (prefetched into registers one plane ahead)].
 // Layers 1 and 2 are implicit GEMMs on mma.sync.m16n8k16 (FP16 operands,
 // FP32 accumulation) with the weights as the 16 x 16 A operand (rows =
 // output channels) and 8 points along x as B; one B fragment serves the
@@ -109,6 +109,22 @@ __device__ __forceinline__ uint32_t s_u32(const void *p) { return (uint32_t)__cv
 // 16-channel activation row; the halves are swapped for points with bit 2
 // set so that 8 consecutive points of an ldmatrix phase hit 8 bank groups.
 __device__ __forceinline__ int act_off(int q, int h) { return q * 32 + ((h ^ ((q >> 2) & 1)) << 4); }
+
+// Epilogue of a 16 (channels) x 8 (points) FP32 accumulator tile: bias,
+// ReLU, zero for points outside the grid, FP16, stored as the 16-channel
+// rows of points q0 .. q0+7 (act_off layout). The lane holds channels g and
+// g+8 of points 2t, 2t+1 -- rows of the two 8 x 8 [channel][point] halves;
+// stmatrix .trans writes their transposes, one point per row.
+__device__ __forceinline__ void store_act_tile(unsigned char *base, int q0, const float *acc, float blo,
+                                               float bhi, bool in0, bool in1, int lane) {
+  const float v00 = in0 ? fmaxf(acc[0] + blo, 0.f) : 0.f, v01 = in1 ? fmaxf(acc[1] + blo, 0.f) : 0.f;
+  const float v10 = in0 ? fmaxf(acc[2] + bhi, 0.f) : 0.f, v11 = in1 ? fmaxf(acc[3] + bhi, 0.f) : 0.f;
+  __half2 h0 = __floats2half2_rn(v00, v01), h1 = __floats2half2_rn(v10, v11);
+  const uint32_t r0 = *reinterpret_cast<uint32_t *>(&h0), r1 = *reinterpret_cast<uint32_t *>(&h1);
+  const uint32_t addr = s_u32(base + act_off(q0 + (lane & 7), (lane >> 3) & 1));
+  asm volatile("stmatrix.sync.aligned.m8n8.x2.trans.shared.b16 [%0], {%1, %2};" ::"r"(addr), "r"(r0), "r"(r1)
+               : "memory");
+}
 
 // A fragment (16 x 16, row-major [m][k] FP16 in shared memory, each row's
 // 16-byte halves placed by act_off) of ldmatrix.x4.
@@ -272,8 +288,37 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
   fetch(z0 - 2);
   __syncthreads();
 
+  // Layer-3 gather of a2 plane p's products (D) into the pending output
+  // planes p+1 (a = 0), p (a = 1), p-1 (a = 2); plane p-1 is then complete
+  // and written out. Runs one iteration after the products, together with
+  // the next plane's layer 1 (two barriers per plane).
+  auto gather = [&](int p) {
+    const float *D = reinterpret_cast<const float *>(sm + OFF_D3);
+    float *O = reinterpret_cast<float *>(sm + OFF_O);
+    for (int i = tid; i < TY * TX; i += NTHR) {
+      const int oy = i / TX, ox = i % TX;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int zo = p + 1 - a;
+        float sacc = 0.f;
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) sacc += D[((a * 3 + b) * 3 + c) * DSTR + (oy + b) * W2R + ox + c];
+        O[(((zo % 3) + 3) % 3) * TY * TX + i] += sacc;
+      }
+      const int zd = p - 1;  // complete
+      float *Od = O + (((zd % 3) + 3) % 3) * TY * TX + i;
+      const int gy = Y0 + oy, gx = X0 + ox;
+      if (zd >= z0 && zd < z1 && gy < NY && gx < NX)
+        out[((size_t)zd * NY + gy) * NX + gx] = fmaf(*Od, bsm[33], bsm[32]);
+      *Od = 0.f;  // the slot is reused for plane p + 2
+    }
+  };
+
   for (int j = 0; j < nit; ++j) {
     const int zi = z0 - 3 + j;  // the newest input plane in the ring
+    if (j >= 5) gather(zi - 3);  // products of the previous iteration's layer-2 plane
     // ---- P1: layer 1 at plane q1 = zi - 1 (input planes q1-1 .. q1+1)
     const int q1 = zi - 1;
     if (j >= 2) {
@@ -317,19 +362,14 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
           }
         }
         // epilogue: bias, ReLU, zero outside the grid, FP16 into the ring
+        const int gx0 = X0 - 2 + sx * 8 + 2 * t4;
+        const bool xin0 = gx0 >= 0 && gx0 < NX, xin1 = gx0 + 1 >= 0 && gx0 + 1 < NX;
+        const float blo = bsm[g], bhi = bsm[g + 8];
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
           const int y1 = yb + r, gy = Y0 - 2 + y1;
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int xq = sx * 8 + 2 * t4 + e, gx = X0 - 2 + xq;
-            const bool in = zin && gy >= 0 && gy < NY && gx >= 0 && gx < NX;
-            const int q = y1 * W1R + xq;
-            const float v0 = in ? fmaxf(acc[r][e] + bsm[g], 0.f) : 0.f;          // channel g
-            const float v1 = in ? fmaxf(acc[r][2 + e] + bsm[g + 8], 0.f) : 0.f;  // channel g + 8
-            *reinterpret_cast<__half *>(a1p + act_off(q, 0) + g * 2) = __float2half_rn(v0);
-            *reinterpret_cast<__half *>(a1p + act_off(q, 1) + g * 2) = __float2half_rn(v1);
-          }
+          const bool yin = zin && gy >= 0 && gy < NY;
+          store_act_tile(a1p, y1 * W1R + sx * 8, acc[r], blo, bhi, yin && xin0, yin && xin1, lane);
         }
       }
     }
@@ -374,18 +414,15 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
             }
           }
         }
+        {
+          const int gx0 = X0 - 1 + sx * 8 + 2 * t4;
+          const bool xin0 = gx0 >= 0 && gx0 < NX, xin1 = gx0 + 1 >= 0 && gx0 + 1 < NX;
+          const float blo = bsm[16 + g], bhi = bsm[16 + g + 8];
 #pragma unroll
-        for (int r = 0; r < RY; ++r) {
-          const int y2 = yb + r, gy = Y0 - 1 + y2;
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int xq = sx * 8 + 2 * t4 + e, gx = X0 - 1 + xq;
-            const bool in = zin && gy >= 0 && gy < NY && gx >= 0 && gx < NX;
-            const int q = y2 * W2R + xq;
-            const float v0 = in ? fmaxf(acc[r][e] + bsm[16 + g], 0.f) : 0.f;
-            const float v1 = in ? fmaxf(acc[r][2 + e] + bsm[16 + g + 8], 0.f) : 0.f;
-            *reinterpret_cast<__half *>(a2p + act_off(q, 0) + g * 2) = __float2half_rn(v0);
-            *reinterpret_cast<__half *>(a2p + act_off(q, 1) + g * 2) = __float2half_rn(v1);
+          for (int r = 0; r < RY; ++r) {
+            const int y2 = yb + r, gy = Y0 - 1 + y2;
+            const bool yin = zin && gy >= 0 && gy < NY;
+            store_act_tile(a2p, y2 * W2R + sx * 8, acc[r], blo, bhi, yin && xin0, yin && xin1, lane);
           }
         }
         // layer-3 products of this warp's own a2 points (the rows of the
@@ -412,43 +449,16 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
         __syncwarp();  // the a2 tile is rewritten by this warp in the next plane
       }
     }
-    __syncthreads();
-
-    // ---- P4: gather the products of a2 plane p = zi - 2 into the pending
-    // output planes p+1 (a = 0), p (a = 1), p-1 (a = 2); plane p-1 is then
-    // complete and written out.
-    if (j >= 4) {
-      const int p = q2;
-      const float *D = reinterpret_cast<const float *>(sm + OFF_D3);
-      float *O = reinterpret_cast<float *>(sm + OFF_O);
-      for (int i = tid; i < TY * TX; i += NTHR) {
-        const int oy = i / TX, ox = i % TX;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          const int zo = p + 1 - a;
-          float sacc = 0.f;
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) sacc += D[((a * 3 + b) * 3 + c) * DSTR + (oy + b) * W2R + ox + c];
-          O[(((zo % 3) + 3) % 3) * TY * TX + i] += sacc;
-        }
-        const int zd = p - 1;  // complete
-        float *Od = O + (((zd % 3) + 3) % 3) * TY * TX + i;
-        const int gy = Y0 + oy, gx = X0 + ox;
-        if (zd >= z0 && zd < z1 && gy < NY && gx < NX)
-          out[((size_t)zd * NY + gy) * NX + gx] = fmaf(*Od, bsm[33], bsm[32]);
-        *Od = 0.f;  // the slot is reused for plane p + 2
-      }
-    }
     // next input plane into the slot of plane zi - 2 (last read by layer 1
-    // of this iteration, two barriers ago), then prefetch the one after
+    // of this iteration, one barrier ago), then prefetch the one after
     if (j + 1 < nit) {
       store(zi + 1);
       if (j + 2 < nit) fetch(zi + 2);
     }
     __syncthreads();
+
   }
+  if (nit - 1 >= 4) gather(z0 - 3 + nit - 1 - 2);  // products of the last layer-2 plane
 }
 
 // ---------------------------------------------------------------------------

@@ -134,3 +134,37 @@ def test_dirichlet_ghosts_symmetric(O):
         a = np.sum(O.laplacian(u, order, 1.0) * v)
         b = np.sum(u * O.laplacian(v, order, 1.0))
         assert abs(a - b) < 1e-10 * abs(a)
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_point_updates_equal_the_full_step(O, order):
+    """The block point updates used to check full-size GPU runs equal the
+    full oracle step at interior points of a grid with a varying medium and
+    sponge (acoustic and TTI)."""
+    rng = np.random.default_rng(order)
+    shape = (14, 15, 16)
+    nb = 3
+    vp = rng.uniform(1500, 3000, shape)
+    eps = rng.uniform(0, 0.3, shape)
+    delta = np.minimum(rng.uniform(0, 0.2, shape), eps)
+    theta = rng.uniform(0, 1.0, shape)
+    phi = rng.uniform(0, 3.0, shape)
+    dt = 1e-3
+    s = O.Setup(vp, 10.0, nb, order, dt, eps=eps, delta=delta, theta=theta, phi=phi)
+    comp = s.shape
+    u, um, q, qm = rng.standard_normal((4,) + comp)
+    up = O.acoustic_step(s, u, um)
+    pp, rp = O.tti_step(s, u, um, q, qm)
+    r = order // 2
+    gam = lambda k, j, i: s.gx[i] + s.gy[j] + s.gz[k]
+    for (k, j, i) in [(r, r, r), (r + 1, 7, 9), (comp[0] - r - 1, comp[1] - r - 1, comp[2] - r - 1),
+                      (10, r, 12), (r, r + 1, r + 2)]:
+        sl = (slice(k - r, k + r + 1), slice(j - r, j + r + 1), slice(i - r, i + r + 1))
+        v_c = np.sqrt(s.c[k, j, i]) / dt
+        a = O.acoustic_update_at(u[sl], um[k, j, i], v_c, gam(k, j, i), s.h, order, dt)
+        assert abs(a - up[k, j, i]) <= 1e-12 * np.abs(u).max()
+        b = O.tti_update_at(u[sl], um[k, j, i], q[sl], qm[k, j, i], v_c, s.eps[k, j, i],
+                            s.delta[k, j, i], s.theta[k, j, i], s.phi[k, j, i], gam(k, j, i), s.h,
+                            order, dt)
+        assert abs(b[0] - pp[k, j, i]) <= 1e-12 * np.abs(u).max()
+        assert abs(b[1] - rp[k, j, i]) <= 1e-12 * np.abs(u).max()
