@@ -15,22 +15,26 @@
 
 namespace fdw {
 
+// One block per row (j, k) of the padded layout, threads along x: the
+// damping of the row is loaded once and no 64-bit division is done per
+// point (that index arithmetic made this per-step kernel issue-bound).
 template <typename T>
 __global__ void grad_accum_kernel(const T *__restrict__ mu, const T *__restrict__ u1,
                                   const T *__restrict__ u0, const T *__restrict__ um1,
                                   float *__restrict__ g32, Dims d, Sponge sp) {
-  const size_t n = d.vol();
-  for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
-       p += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(p % d.Xp);
-    if (i >= d.NX) continue;
-    const size_t rest = p / d.Xp;
-    const int j = (int)(rest % d.NY), k = (int)(rest / d.NY);
-    const float gh = sp.gx[i] + sp.gy[j] + sp.gz[k];
-    const float a = St<T>::ld(mu[p]);
-    const float b = (1.f + gh) * St<T>::ld(u1[p]) - 2.f * St<T>::ld(u0[p]) +
-                    (um1 ? (1.f - gh) * St<T>::ld(um1[p]) : 0.f);
-    g32[p] = fmaf(a, b, g32[p]);
+  const int rows = d.NY * d.NZ;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % d.NY, k = row / d.NY;
+    const float gyz = sp.gy[j] + sp.gz[k];
+    const size_t base = (size_t)row * d.Xp;
+    for (int i = threadIdx.x; i < d.NX; i += blockDim.x) {
+      const size_t p = base + i;
+      const float gh = sp.gx[i] + gyz;
+      const float a = St<T>::ld(mu[p]);
+      const float b = (1.f + gh) * St<T>::ld(u1[p]) - 2.f * St<T>::ld(u0[p]) +
+                      (um1 ? (1.f - gh) * St<T>::ld(um1[p]) : 0.f);
+      g32[p] = fmaf(a, b, g32[p]);
+    }
   }
 }
 
@@ -68,20 +72,25 @@ static int grid_for(size_t n) {
   return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
 }
 
+static int row_grid(const Dims &d) {
+  const long r = (long)d.NY * d.NZ;
+  return (int)(r < 152 * 64 ? (r < 1 ? 1 : r) : 152 * 64);
+}
+
 cudaError_t launch_grad_accum(int storage, const void *mu, const void *u1, const void *u0,
                               const void *um1, float *g32, Dims d, Sponge sp, cudaStream_t st) {
   switch (storage) {
     case FDW_F32:
-      grad_accum_kernel<float><<<grid_for(d.vol()), 256, 0, st>>>(
+      grad_accum_kernel<float><<<row_grid(d), 256, 0, st>>>(
           (const float *)mu, (const float *)u1, (const float *)u0, (const float *)um1, g32, d, sp);
       break;
     case FDW_BF16:
-      grad_accum_kernel<__nv_bfloat16><<<grid_for(d.vol()), 256, 0, st>>>(
+      grad_accum_kernel<__nv_bfloat16><<<row_grid(d), 256, 0, st>>>(
           (const __nv_bfloat16 *)mu, (const __nv_bfloat16 *)u1, (const __nv_bfloat16 *)u0,
           (const __nv_bfloat16 *)um1, g32, d, sp);
       break;
     case FDW_F16:
-      grad_accum_kernel<__half><<<grid_for(d.vol()), 256, 0, st>>>(
+      grad_accum_kernel<__half><<<row_grid(d), 256, 0, st>>>(
           (const __half *)mu, (const __half *)u1, (const __half *)u0, (const __half *)um1, g32, d, sp);
       break;
     default: return cudaErrorInvalidValue;

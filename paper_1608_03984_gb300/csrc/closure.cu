@@ -501,17 +501,16 @@ __global__ void closure_apply_out_kernel(const float *__restrict__ net, const fl
                                          const float *__restrict__ s_dev, T *__restrict__ u, Dims d, int nb,
                                          int nx, int ny, int nz) {
   const float s = *s_dev;
-  const long long vol = (long long)d.NX * d.NY * d.NZ;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < vol;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(q % d.NX);
-    const long long r = q / d.NX;
-    const int y = (int)(r % d.NY), z = (int)(r / d.NY);
-    if (x < nb + kHalo || x >= nb + nx - kHalo || y < nb + kHalo || y >= nb + ny - kHalo ||
-        z < nb + kHalo || z >= nb + nz - kHalo)
-      continue;
-    const size_t pp = ((size_t)z * d.NY + y) * d.Xp + x;
-    u[pp] = St<T>::st(St<T>::ld(u[pp]) + s * (net[q] - base[q]));
+  // rows (j, k) whose points can be corrected; one block per row
+  const int y0 = nb + kHalo, y1 = nb + ny - kHalo, z0 = nb + kHalo, z1 = nb + nz - kHalo;
+  const int x0 = nb + kHalo, x1 = nb + nx - kHalo;
+  const int ry = y1 - y0, rz = z1 - z0;
+  if (ry <= 0 || rz <= 0 || x1 <= x0) return;
+  for (int row = blockIdx.x; row < ry * rz; row += gridDim.x) {
+    const int y = y0 + row % ry, z = z0 + row / ry;
+    const size_t q0 = ((size_t)z * d.NY + y) * d.NX, p0 = ((size_t)z * d.NY + y) * d.Xp;
+    for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x)
+      u[p0 + x] = St<T>::st(St<T>::ld(u[p0 + x]) + s * (net[q0 + x] - base[q0 + x]));
   }
 }
 

@@ -185,21 +185,20 @@ __global__ void tc_inputs_kernel(const T *__restrict__ u, const T *__restrict__ 
                                  const float *__restrict__ vp, int nx, int ny, int nz, int nb, Dims d,
                                  const float *__restrict__ s_dev, uint2 *__restrict__ x16) {
   const float inv = u ? 1.f / *s_dev : 0.f;
-  const long long n = (long long)d.NX * d.NY * d.NZ;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-       q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % d.NX);
-    const long long r = q / d.NX;
-    const int j = (int)(r % d.NY), k = (int)(r / d.NY);
-    const size_t p = ((size_t)k * d.NY + j) * d.Xp + i;
-    const int pi = min(max(i - nb, 0), nx - 1), pj = min(max(j - nb, 0), ny - 1), pk = min(max(k - nb, 0), nz - 1);
-    const float v = (vp[((size_t)pk * ny + pj) * nx + pi] - 3000.f) / 750.f;
-    const float a = u ? St<T>::ld(u[p]) * inv : 0.f, b = u ? St<T>::ld(um[p]) * inv : 0.f;
-    __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(v, 0.f);
-    uint2 o;
-    o.x = *reinterpret_cast<uint32_t *>(&lo);
-    o.y = *reinterpret_cast<uint32_t *>(&hi);
-    x16[q] = o;
+  const int rows = d.NY * d.NZ;  // one block per row: no 64-bit division per point
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = row % d.NY, k = row / d.NY;
+    const float *vr = vp + ((size_t)min(max(k - nb, 0), nz - 1) * ny + min(max(j - nb, 0), ny - 1)) * nx;
+    for (int i = threadIdx.x; i < d.NX; i += blockDim.x) {
+      const size_t p = (size_t)row * d.Xp + i;
+      const float v = (vr[min(max(i - nb, 0), nx - 1)] - 3000.f) / 750.f;
+      const float a = u ? St<T>::ld(u[p]) * inv : 0.f, b = u ? St<T>::ld(um[p]) * inv : 0.f;
+      __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(v, 0.f);
+      uint2 o;
+      o.x = *reinterpret_cast<uint32_t *>(&lo);
+      o.y = *reinterpret_cast<uint32_t *>(&hi);
+      x16[(size_t)row * d.NX + i] = o;
+    }
   }
 }
 
@@ -500,7 +499,9 @@ template <typename T>
 static cudaError_t tc_net(ClosureNet *c, const T *u, const T *um, const float *vp, int nx, int ny, int nz, int nb,
                           Dims d, float *dst, cudaStream_t st) {
   const long long vol = (long long)d.NX * d.NY * d.NZ;
-  tc_inputs_kernel<T><<<tc_grid_for(vol), 256, 0, st>>>(u, um, vp, nx, ny, nz, nb, d, c->s_dev, (uint2 *)c->x16);
+  const long rows = (long)d.NY * d.NZ;
+  tc_inputs_kernel<T><<<(int)(rows < 152 * 64 ? rows : 152 * 64), 256, 0, st>>>(u, um, vp, nx, ny, nz, nb, d,
+                                                                                c->s_dev, (uint2 *)c->x16);
   const int tiles = ((d.NX + tc::TX - 1) / tc::TX) * ((d.NY + tc::TY - 1) / tc::TY);
   int zch = (2 * 152 + tiles - 1) / tiles;  // about two CTAs per SM in total
   if (zch < 1) zch = 1;
