@@ -245,6 +245,31 @@ class PatchSampler:
         return X, T
 
 
+class PatchBank:
+    """Patches drawn once from many models' samplers (whose full fields are
+    then dropped), served uniformly at random: the training set of many
+    models in a fraction of the memory. Callable like a PatchSampler."""
+
+    def __init__(self):
+        self.X, self.T = [], []
+
+    def add(self, sampler, count, gen):
+        X, T = sampler(count, gen)
+        self.X.append(X)
+        self.T.append(T)
+
+    def freeze(self):
+        self.X, self.T = torch.cat(self.X), torch.cat(self.T)
+        return self
+
+    def __len__(self):
+        return int(self.X.shape[0])
+
+    def __call__(self, count, gen):
+        idx = torch.randint(0, self.X.shape[0], (count,), generator=gen, device=self.X.device)
+        return self.X[idx].contiguous(), self.T[idx].contiguous()
+
+
 def target_scale(samplers, gen, count=512):
     """Power of two K that brings the patches' RMS target near one. The
     defect of one coarse step is ~1e-4 of max |u|: trained on K * target
