@@ -12,8 +12,8 @@ namespace fdw {
 // One thread per point, plain global loads with bounds checks.
 template <typename T, int R>
 __global__ void __launch_bounds__(256)
-    acoustic_naive_kernel(const T *__restrict__ cur, T *__restrict__ prev,
-                          const T *__restrict__ c, Dims d, Weights w, Sponge sp) {
+    acoustic_naive_kernel(const T *cur, const T *prev, T *out, const T *__restrict__ c, Dims d, Weights w,
+                          Sponge sp) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
   const int z = blockIdx.z;
@@ -36,14 +36,15 @@ __global__ void __launch_bounds__(256)
   const float gh = sp.gx[x] + sp.gy[y] + sp.gz[z];
   const float up =
       (2.f * uc - (1.f - gh) * St<T>::ld(prev[p]) + St<T>::ld(c[p]) * lap) * __frcp_rn(1.f + gh);
-  prev[p] = St<T>::st(up);
+  out[p] = St<T>::st(up);
 }
 
 template <typename T, int R>
 static cudaError_t launch_naive_r(const AcousticLaunch &L, cudaStream_t st) {
   dim3 blk(32, 8), grd((L.d.NX + 31) / 32, (L.d.NY + 7) / 8, L.d.NZ);
-  acoustic_naive_kernel<T, R><<<grd, blk, 0, st>>>((const T *)L.cur, (T *)L.prev, (const T *)L.c,
-                                                   L.d, L.w, L.sp);
+  acoustic_naive_kernel<T, R><<<grd, blk, 0, st>>>((const T *)L.cur, (const T *)L.prev,
+                                                   (T *)(L.out ? L.out : L.prev), (const T *)L.c, L.d, L.w,
+                                                   L.sp);
   return cudaGetLastError();
 }
 

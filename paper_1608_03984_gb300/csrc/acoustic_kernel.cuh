@@ -280,7 +280,7 @@ cudaError_t launch_acoustic_cfg(const AcousticLaunch &L, cudaStream_t st) {
   dim3 grd((L.d.NX + C::TX - 1) / C::TX, (L.d.NY + C::TY - 1) / C::TY, (L.d.NZ + zc - 1) / zc);
   dim3 blk(32, BY);
   kern<<<grd, blk, C::SMEM_B, st>>>(*L.map_cur_halo, *L.map_cur_int, *L.map_prev_int, *L.map_c_int,
-                                     (T *)L.prev, L.d, L.w, L.sp, zc, L.err);
+                                     (T *)(L.out ? L.out : L.prev), L.d, L.w, L.sp, zc, L.err);
   return cudaGetLastError();
 }
 

@@ -121,6 +121,7 @@ struct fdw_solver {
   // forward history ring (levels of u for the gradient)
   std::vector<void *> hist;
   std::vector<int> hist_level;
+  std::vector<CUtensorMap> hmap_halo, hmap_int;  // tensor maps of the ring buffers
   bool hist_on = false;
 };
 
@@ -766,6 +767,72 @@ static int ensure_graphs(fdw_solver *s) {
   return FDW_OK;
 }
 
+static int hist_slot_of(const fdw_solver *s, int lvl) {
+  const int H = (int)s->hist.size();
+  return ((lvl % H) + H) % H;
+}
+
+// Steps with the history on (acoustic): level n+1 is written straight into
+// its ring slot from the slots of levels n and n-1 (no per-step copy); the
+// solver's own two buffers receive the last two levels at the end.
+static int step_into_history(fdw_solver *s, int nsteps) {
+  CK(acoustic_prepare(s->storage, s->r, s->tile));
+  for (int n = 0; n < nsteps; ++n) {
+    const int lc = s->it + n, sc = hist_slot_of(s, lc), sp = hist_slot_of(s, lc - 1),
+              sn = hist_slot_of(s, lc + 1);
+    if (s->hist_level[sc] != lc || s->hist_level[sp] != lc - 1)
+      return fail(FDW_ERR_STATE, "history lost levels %d, %d", lc, lc - 1);
+    AcousticLaunch L{};
+    L.storage = s->storage;
+    L.r = s->r;
+    L.d = s->d;
+    L.w = s->w;
+    L.sp = Sponge{s->gam[0], s->gam[1], s->gam[2]};
+    L.cur = s->hist[sc];
+    L.prev = s->hist[sp];
+    L.out = s->hist[sn];
+    L.c = s->c;
+    L.map_cur_halo = &s->hmap_halo[sc];
+    L.map_cur_int = &s->hmap_int[sc];
+    L.map_prev_int = &s->hmap_int[sp];
+    L.map_c_int = &s->map_c;
+    L.zchunks = s->zchunks;
+    L.err = s->d_err;
+    L.naive = s->naive;
+    L.tile = s->tile;
+    CK(launch_acoustic(L, s->stream));
+    SparseLaunch S{};
+    memset(&S, 0, sizeof S);
+    S.storage = s->storage;
+    S.d = s->d;
+    S.sp = L.sp;
+    S.f0 = s->hist[sn];
+    S.c = s->c;
+    S.nsrc = s->nsrc;
+    S.src_corner = s->src_corner;
+    S.src_w = s->src_w;
+    S.wavelet = s->wavelet;
+    S.amp_scale = (float)s->fscale;
+    S.trace_scale = 1.0 / s->fscale;
+    S.nt_src = s->nt_src;
+    S.nrec = s->nrec;
+    S.rec_corner = s->rec_corner;
+    S.rec_w = s->rec_w;
+    S.traces = s->traces;
+    S.nt_rec = s->nt_rec;
+    S.step = s->d_step;
+    CK(launch_sparse(S, s->stream));
+    s->hist_level[sn] = lc + 1;
+  }
+  const size_t fb = s->d.vol() * s->el;
+  const int last = s->it + nsteps;
+  CK(cudaMemcpyAsync(s->f[0][s->cur], s->hist[hist_slot_of(s, last)], fb, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->f[0][1 - s->cur], s->hist[hist_slot_of(s, last - 1)], fb, cudaMemcpyDeviceToDevice,
+                     s->stream));
+  s->it += nsteps;
+  return FDW_OK;
+}
+
 extern "C" int fdw_step(fdw_solver *s, int nsteps) {
   if (!s) return fail(FDW_ERR_INVALID_ARG, "NULL solver");
   if (nsteps < 0) return fail(FDW_ERR_INVALID_ARG, "nsteps < 0");
@@ -774,6 +841,7 @@ extern "C" int fdw_step(fdw_solver *s, int nsteps) {
   DeviceGuard g(s->device);
   int rc = ensure_graphs(s);
   if (rc) return rc;
+  if (s->hist_on && !s->prof && s->eq == FDW_ACOUSTIC) return step_into_history(s, nsteps);
   const size_t fb = s->d.vol() * s->el;
   for (int n = 0; n < nsteps; ++n) {
     if (s->prof && (size_t)(2 * s->prof_n + 1) < s->ev.size()) {
@@ -835,6 +903,16 @@ extern "C" int fdw_history_begin(fdw_solver *s, int nlevels) {
   CK(cudaMemcpyAsync(s->hist[s1], s->f[0][1 - s->cur], fb, cudaMemcpyDeviceToDevice, s->stream));
   s->hist_level[s0] = l0;
   s->hist_level[s1] = l1;
+  // the stencil reads and writes the ring buffers directly (fdw_step)
+  TileGeom tg;
+  if (acoustic_geom(s->storage, s->r, s->tile, &tg)) return fail(FDW_ERR_INVALID_ARG, "bad tile");
+  s->hmap_halo.resize(s->hist.size());
+  s->hmap_int.resize(s->hist.size());
+  for (size_t i = 0; i < s->hist.size(); ++i) {
+    int rc = make_map(&s->hmap_halo[i], s, s->hist[i], tg.box_halo_x, tg.box_halo_y);
+    if (!rc) rc = make_map(&s->hmap_int[i], s, s->hist[i], tg.box_int_x, tg.box_int_y);
+    if (rc) return rc;
+  }
   s->hist_on = true;
   return FDW_OK;
 }

@@ -70,6 +70,7 @@ struct AcousticLaunch {
   Weights w;
   Sponge sp;
   void *cur, *prev;       // fields (element type = storage)
+  void *out;              // buffer of level n+1 (null: prev's storage, in place)
   const void *c;          // coefficient (storage type)
   const CUtensorMap *map_cur_halo, *map_cur_int, *map_prev_int, *map_c_int;
   int zchunks;            // CTAs along z
