@@ -44,6 +44,28 @@ struct ConvGeom {
   __host__ __device__ long long out_vol() const { return (long long)zo * yo * xo; }
 };
 
+// (x, y, z, b) of a linear index over [B][zd][yd][xd]; 32-bit division
+// when the index fits (every use here), 64-bit otherwise.
+__device__ __forceinline__ void split_index(long long q, int xd, int yd, int zd, int &x, int &y, int &z,
+                                            int &b) {
+  if (q <= 0x7fffffffLL) {
+    unsigned u = (unsigned)q;
+    x = (int)(u % (unsigned)xd);
+    u /= (unsigned)xd;
+    y = (int)(u % (unsigned)yd);
+    u /= (unsigned)yd;
+    z = (int)(u % (unsigned)zd);
+    b = (int)(u / (unsigned)zd);
+  } else {
+    x = (int)(q % xd);
+    long long r = q / xd;
+    y = (int)(r % yd);
+    r /= yd;
+    z = (int)(r % zd);
+    b = (int)(r / zd);
+  }
+}
+
 template <int CI, int CO, bool RELU>
 __global__ void __launch_bounds__(256)
     conv_fwd_kernel(const float *__restrict__ in, const __nv_bfloat16 *__restrict__ w,
@@ -54,12 +76,8 @@ __global__ void __launch_bounds__(256)
   const long long nout = (long long)g.B * g.out_vol();
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nout;
        q += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(q % g.xo);
-    long long r = q / g.xo;
-    const int y = (int)(r % g.yo);
-    r /= g.yo;
-    const int z = (int)(r % g.zo);
-    const int b = (int)(r / g.zo);
+    int x, y, z, b;
+    split_index(q, g.xo, g.yo, g.zo, x, y, z, b);
     float acc[CO];
 #pragma unroll
     for (int o = 0; o < CO; ++o) acc[o] = bias[o];
@@ -105,12 +123,8 @@ __global__ void __launch_bounds__(256)
   const long long nin = (long long)g.B * g.in_vol();
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nin;
        q += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(q % g.xi);
-    long long r = q / g.xi;
-    const int y = (int)(r % g.yi);
-    r /= g.yi;
-    const int z = (int)(r % g.zi);
-    const int b = (int)(r / g.zi);
+    int x, y, z, b;
+    split_index(q, g.xi, g.yi, g.zi, x, y, z, b);
     float acc[CI];
 #pragma unroll
     for (int i = 0; i < CI; ++i) acc[i] = 0.f;
@@ -163,12 +177,8 @@ __global__ void __launch_bounds__(256)
   const long long per = (nout + gridDim.y - 1) / gridDim.y;
   const long long q0 = (long long)chunk * per, q1 = q0 + per < nout ? q0 + per : nout;
   for (long long q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-    const int x = (int)(q % g.xo);
-    long long r = q / g.xo;
-    const int y = (int)(r % g.yo);
-    r /= g.yo;
-    const int z = (int)(r % g.zo);
-    const int b = (int)(r / g.zo);
+    int x, y, z, b;
+    split_index(q, g.xo, g.yo, g.zo, x, y, z, b);
     const float gv = gout[((long long)b * CO + o) * g.out_vol() + ((long long)z * g.yo + y) * g.xo + x];
     const float *inb = in + ((long long)b * CI + i) * g.in_vol();
 #pragma unroll
