@@ -113,15 +113,12 @@ int acoustic_geom(int storage, int r, int tile, TileGeom *g) {
   }
 }
 
-// Fastest configuration per radius on the 592^3 workload (FP32), from a
-// sweep of all configurations and z chunkings (radii 3, 5 and 7
-// interpolated from their neighbours).
-// Default configuration per (storage, radius), from sweeps of the 592^3
-// workload (FP32 all orders; 16-bit storage orders 2, 4 and 8, FP32's
-// choice above).
+// Default configuration per (storage, radius): the fastest on the 592^3
+// workload in sweeps of every configuration and z chunking at orders 2, 4,
+// 8, 12 and 16 (radii 3, 5 and 7 take a neighbour's choice).
 int acoustic_default_tile(int storage, int r) {
-  static const int best32[kMaxR + 1] = {1, 1, 3, 1, 1, 3, 3, 2, 2};
-  static const int best16[kMaxR + 1] = {1, 1, 1, 1, 4, 3, 3, 2, 2};
+  static const int best32[kMaxR + 1] = {1, 1, 3, 1, 1, 3, 3, 3, 1};
+  static const int best16[kMaxR + 1] = {1, 1, 1, 1, 1, 5, 5, 1, 1};
   if (r < 1 || r > kMaxR) return 1;
   return storage == FDW_F32 ? best32[r] : best16[r];
 }

@@ -37,6 +37,33 @@ template <typename T, int N> struct alignas(sizeof(T) * N) Vec {
   T v[N];
 };
 
+// Packed FP32 arithmetic. With an even number of x points per thread the
+// kernel handles them in pairs through the f32x2 instructions (__ffma2_rn,
+// __fadd2_rn, __fmul2_rn: per component the rounding of the scalar
+// operation), halving the issue slots of the stencil arithmetic, which is
+// what bounds the high orders. Pk<1> is the scalar fallback (RX = 1).
+template <int W> struct Pk;
+template <> struct Pk<1> {
+  using E = float;
+  static __device__ __forceinline__ E fma(E a, E b, E c) { return fmaf(a, b, c); }
+  static __device__ __forceinline__ E add(E a, E b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ E mul(E a, E b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ E splat(float a) { return a; }
+  static __device__ __forceinline__ E make(float a, float) { return a; }
+  static __device__ __forceinline__ float &at(E &e, int) { return e; }
+  static __device__ __forceinline__ E wt(const Weights &w, int m) { return w.w2[m]; }
+};
+template <> struct Pk<2> {
+  using E = float2;
+  static __device__ __forceinline__ E fma(E a, E b, E c) { return __ffma2_rn(a, b, c); }
+  static __device__ __forceinline__ E add(E a, E b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ E mul(E a, E b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ E splat(float a) { return make_float2(a, a); }
+  static __device__ __forceinline__ E make(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ float &at(E &e, int i) { return i ? e.y : e.x; }
+  static __device__ __forceinline__ E wt(const Weights &w, int m) { return w.w2p[m]; }
+};
+
 template <typename T, int R, int RX, int RY, int BY, int NS, int U>
 struct AcTile {
   static constexpr int TX = 32 * RX;
@@ -131,17 +158,23 @@ __global__ void __launch_bounds__(32 * BY)
     for (int j = 0; j < n0; ++j) issue(j);
   }
 
-  // q[ry][rx][s]: slots u..u+2R hold planes zh+u-2R .. zh+u during
+  // Points are handled in packs of W (pairs when RX is even): pack k holds
+  // x points W k .. W k + W - 1 of the thread's row segment.
+  constexpr int W = (RX % 2 == 0) ? 2 : 1;
+  constexpr int NK = RX / W;
+  using P = Pk<W>;
+  using E = typename P::E;
+  // q[ry][k][s]: slots u..u+2R hold planes zh+u-2R .. zh+u during
   // sub-iteration u of a group of U planes.
-  float q[RY][RX][C::QL];
+  E q[RY][NK][C::QL];
 #pragma unroll
   for (int ry = 0; ry < RY; ++ry)
 #pragma unroll
-    for (int rx = 0; rx < RX; ++rx)
+    for (int k = 0; k < NK; ++k)
 #pragma unroll
-      for (int i = 0; i < C::QL; ++i) q[ry][rx][i] = 0.f;
+      for (int i = 0; i < C::QL; ++i) q[ry][k][i] = P::splat(0.f);
 
-  const float wc = 3.f * w.w2[0];
+  const E wc = P::splat(3.f * w.w2[0]);
   const size_t plane = d.plane();
 
 #pragma unroll 1
@@ -172,7 +205,9 @@ __global__ void __launch_bounds__(32 * BY)
         V v;
         if (head) v = *(const V *)(hd + (ty * RY + ry) * C::TX + xl);
 #pragma unroll
-        for (int rx = 0; rx < RX; ++rx) q[ry][rx][2 * R + u] = head ? St<T>::ld(v.v[rx]) : 0.f;
+        for (int k = 0; k < NK; ++k)
+          q[ry][k][2 * R + u] =
+              head ? P::make(St<T>::ld(v.v[W * k]), St<T>::ld(v.v[W * k + W - 1])) : P::splat(0.f);
       }
       if (j < 2 * R) continue;
 
@@ -181,16 +216,17 @@ __global__ void __launch_bounds__(32 * BY)
       const T *PV = (const T *)(st + C::HALO_B + C::INT_B);
       const T *CC = (const T *)(st + C::HALO_B + 2 * C::INT_B);
 
-      float acc[RY][RX];
+      E acc[RY][NK];
       // z direction and centre, from the queue
 #pragma unroll
       for (int ry = 0; ry < RY; ++ry)
 #pragma unroll
-        for (int rx = 0; rx < RX; ++rx) {
-          float a = wc * q[ry][rx][u + R];
+        for (int k = 0; k < NK; ++k) {
+          E a = P::mul(wc, q[ry][k][u + R]);
 #pragma unroll
-          for (int m = 1; m <= R; ++m) a = fmaf(w.w2[m], q[ry][rx][u + R + m] + q[ry][rx][u + R - m], a);
-          acc[ry][rx] = a;
+          for (int m = 1; m <= R; ++m)
+            a = P::fma(P::wt(w, m), P::add(q[ry][k][u + R + m], q[ry][k][u + R - m]), a);
+          acc[ry][k] = a;
         }
       // y direction: rows ty RY - R .. ty RY + RY - 1 + R of the halo tile
 #pragma unroll
@@ -201,11 +237,15 @@ __global__ void __launch_bounds__(32 * BY)
           const int m = t - ry < 0 ? ry - t : t - ry;
           if (m >= 1 && m <= R) {
 #pragma unroll
-            for (int rx = 0; rx < RX; ++rx) acc[ry][rx] = fmaf(w.w2[m], St<T>::ld(v.v[rx]), acc[ry][rx]);
+            for (int k = 0; k < NK; ++k)
+              acc[ry][k] = P::fma(P::wt(w, m), P::make(St<T>::ld(v.v[W * k]), St<T>::ld(v.v[W * k + W - 1])),
+                                  acc[ry][k]);
           }
         }
       }
-      // x direction: the row segment of each of the thread's rows
+      // x direction: the row segment of each of the thread's rows. Taps at
+      // an even distance pair up aligned elements (x_e, x_e+1) with the
+      // points (W k, W k + 1); odd distances go component by component.
 #pragma unroll
       for (int ry = 0; ry < RY; ++ry) {
         const T *row = H + (ty * RY + ry + R) * C::BXH + C::HX + xl;
@@ -213,12 +253,29 @@ __global__ void __launch_bounds__(32 * BY)
         for (int o = -C::RR; o < RX + C::RR; o += RX) {
           const V v = *(const V *)(row + o);
 #pragma unroll
-          for (int e = 0; e < RX; ++e) {
+          for (int e = 0; e < RX; e += W) {
 #pragma unroll
-            for (int rx = 0; rx < RX; ++rx) {
-              const int t = o + e - rx;
+            for (int k = 0; k < NK; ++k) {
+              const int t = o + e - W * k;
               const int m = t < 0 ? -t : t;
-              if (m >= 1 && m <= R) acc[ry][rx] = fmaf(w.w2[m], St<T>::ld(v.v[e]), acc[ry][rx]);
+              if (m >= 1 && m <= R)
+                acc[ry][k] = P::fma(P::wt(w, m), P::make(St<T>::ld(v.v[e]), St<T>::ld(v.v[e + W - 1])),
+                                    acc[ry][k]);
+            }
+          }
+          if constexpr (W == 2) {
+#pragma unroll
+            for (int e = 0; e < RX; ++e) {
+#pragma unroll
+              for (int k = 0; k < NK; ++k) {
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                  const int t = o + e - 2 * k - i;
+                  const int m = t < 0 ? -t : t;
+                  if ((m & 1) && m <= R)
+                    P::at(acc[ry][k], i) = fmaf(w.w2[m], St<T>::ld(v.v[e]), P::at(acc[ry][k], i));
+                }
+              }
             }
           }
         }
@@ -235,8 +292,9 @@ __global__ void __launch_bounds__(32 * BY)
 #pragma unroll
         for (int rx = 0; rx < RX; ++rx) {
           const float gh = gxr[rx] + gyr[ry] + ghz;
-          const float uc = q[ry][rx][u + R];
-          const float up = (2.f * uc - (1.f - gh) * St<T>::ld(vm.v[rx]) + St<T>::ld(vc.v[rx]) * acc[ry][rx]) *
+          const float uc = P::at(q[ry][rx / W][u + R], rx % W);
+          const float up = (2.f * uc - (1.f - gh) * St<T>::ld(vm.v[rx]) +
+                            St<T>::ld(vc.v[rx]) * P::at(acc[ry][rx / W], rx % W)) *
                            __fdividef(1.f, 1.f + gh);
           res.v[rx] = St<T>::st(up);
         }
@@ -257,9 +315,9 @@ __global__ void __launch_bounds__(32 * BY)
 #pragma unroll
     for (int ry = 0; ry < RY; ++ry)
 #pragma unroll
-      for (int rx = 0; rx < RX; ++rx)
+      for (int k = 0; k < NK; ++k)
 #pragma unroll
-        for (int i = 0; i < 2 * R; ++i) q[ry][rx][i] = q[ry][rx][i + U];
+        for (int i = 0; i < 2 * R; ++i) q[ry][k][i] = q[ry][k][i + U];
   }
 }
 
@@ -300,7 +358,8 @@ void tile_cfg(TileGeom *g) {
   X(1, 4, 2, 4, 4)     \
   X(2, 4, 1, 8, 4)     \
   X(3, 2, 2, 8, 4)     \
-  X(4, 4, 2, 8, 2)
+  X(4, 4, 2, 8, 2)     \
+  X(5, 4, 2, 4, 2)
 constexpr int kAcNS = 4;
 
 // Per-storage dispatch over radius and configuration (one TU per storage).

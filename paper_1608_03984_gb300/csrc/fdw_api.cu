@@ -501,6 +501,7 @@ extern "C" int fdw_create(fdw_solver **out, int nx, int ny, int nz, double h, in
     for (int j = 0; j <= kMaxR; ++j) {
       s->w.w2[j] = j <= s->r ? (float)w2[j] : 0.f;
       s->w.c1[j] = j <= s->r ? (float)c1[j] : 0.f;
+      s->w.w2p[j] = make_float2(s->w.w2[j], s->w.w2[j]);
     }
   }
   int rc = FDW_OK;

@@ -31,8 +31,9 @@ struct Dims {
 
 // Central finite-difference weights at unit spacing, offsets 0..r.
 struct Weights {
-  float w2[kMaxR + 1];  // second derivative
-  float c1[kMaxR + 1];  // first derivative (c1[0] = 0)
+  float w2[kMaxR + 1];    // second derivative
+  float c1[kMaxR + 1];    // first derivative (c1[0] = 0)
+  float2 w2p[kMaxR + 1];  // w2 as pairs {w2, w2}, for packed FP32 arithmetic
 };
 
 // Damping tables: gh_a[i] = gamma_a(i) * dt / 2 for each axis.
@@ -91,7 +92,7 @@ int tti_ctas_per_sm(int storage, int r, int tile);
 struct TileGeom {
   int box_halo_x, box_halo_y, box_int_x, box_int_y, smem;
 };
-constexpr int kAcTiles = 5;  // number of configurations (see acoustic_kernel.cuh)
+constexpr int kAcTiles = 6;  // number of configurations (see acoustic_kernel.cuh)
 // 0 on success, -1 for an unknown (storage, r, tile).
 int acoustic_geom(int storage, int r, int tile, TileGeom *g);
 // Default configuration for (storage, r).
