@@ -598,6 +598,16 @@ def run_closure(args):
     err = {m: {k: float(np.mean([r[m][k] for r in evals])) for k in ("field", "traces")}
            for m in ("coarse", "closure")}
     better = {k: int(sum(r["closure"][k] < r["coarse"][k] for r in evals)) for k in ("field", "traces")}
+    # per-model error ratios (closure / coarse): the median is not moved by one bad model
+    ratio = {k: float(np.median([r["closure"][k] / r["coarse"][k] for r in evals])) for k in ("field", "traces")}
+    depths = sorted(evals[0]["coarse"]["traces_by_depth"])
+    by_depth = {str(dep): {m: float(np.mean([r[m]["traces_by_depth"][dep] for r in evals]))
+                           for m in ("coarse", "closure")} for dep in depths}
+    for dep in depths:
+        by_depth[str(dep)]["median_ratio"] = float(np.median(
+            [r["closure"]["traces_by_depth"][dep] / r["coarse"]["traces_by_depth"][dep] for r in evals]))
+        by_depth[str(dep)]["models_improved"] = int(sum(
+            r["closure"]["traces_by_depth"][dep] < r["coarse"]["traces_by_depth"][dep] for r in evals))
     k1 = pr.source_steps()
     return {"workload": "fine %d^3 + %d-pt sponge h=%g order %d, %d steps; coarse %d^3 + %d-pt sponge "
                         "h=%g order %d, %d steps (closure after step %d); %d held-out models; trained "
@@ -605,7 +615,8 @@ def run_closure(args):
                             pr.n_f, pr.nb_f, pr.h_f, pr.order_f, 2 * nt, pr.n_c, pr.nb_c, pr.h_c,
                             pr.order_c, nt, k1, args.closure_eval, args.closure_models, tr.n_c,
                             args.closure_patches),
-            "error_vs_fine": err, "models_improved": better, "ms": ms,
+            "error_vs_fine": err, "models_improved": better, "median_error_ratio": ratio,
+            "traces_by_depth_m": {str(int(d) * int(pr.h_c)): v for d, v in by_depth.items()}, "ms": ms,
             "speedup_vs_fine": {"coarse": ms["fine"] / ms["coarse"], "closure": ms["fine"] / ms["closure"]},
             "closure_ms_per_step": (ms["closure"] - ms["coarse"] * k1 / nt) / (nt - k1),
             "coarse_ms_per_step": ms["coarse"] / nt,

@@ -326,27 +326,34 @@ def unexplained(net: "fdwave.Closure", sampler, count=512, seed=1):
     return float(loss) / float((T.double() ** 2).mean())
 
 
-def receivers(pr: Pairing, nside=8):
-    """A nside x nside grid of receivers at 5 coarse spacings depth (below
-    the 3-point band next to the sponge that the closure leaves alone), on
-    points of both grids."""
+TRACE_DEPTHS = (5, 10, 20)  # receiver depths in coarse spacings; the first is the headline
+
+
+def receivers(pr: Pairing, nside=8, depths=(5,)):
+    """nside x nside grids of receivers at the given depths in coarse
+    spacings (5: just below the 3-point band next to the sponge that the
+    closure leaves alone), on points of both grids; one grid after the
+    other, in the order of `depths`."""
     span = (pr.n_c - 1) * pr.h_c
     g = np.round(np.linspace(0.1 * span, 0.9 * span, nside) / pr.h_c) * pr.h_c
     X, Y = np.meshgrid(g, g)
-    return np.stack([X.ravel(), Y.ravel(), np.full(X.size, 5 * pr.h_c)], axis=1)
+    return np.concatenate([np.stack([X.ravel(), Y.ravel(), np.full(X.size, dep * pr.h_c)], axis=1)
+                           for dep in depths])
 
 
 def evaluate(pr: Pairing, net, seed: int, nt_c: int, timing=False, closure_from=None):
     """Relative L2 errors of the coarse run alone and with the closure
     against the restricted fine run: final level (physical part) and traces
-    (receivers of `receivers`, fine traces at the coarse times). The
-    closure run takes plain steps until `closure_from` (default: the end of
-    the source, pr.source_steps()), then closure steps. With timing=True
-    also the device milliseconds of each run."""
+    (receivers of `receivers` at 5 coarse spacings depth, fine traces at
+    the coarse times; `traces_by_depth` repeats it for every depth of
+    TRACE_DEPTHS). The closure run takes plain steps until `closure_from`
+    (default: the end of the source, pr.source_steps()), then closure
+    steps. With timing=True also the device milliseconds of each run."""
     k1 = pr.source_steps() if closure_from is None else int(closure_from)
     k1 = min(max(k1, 0), nt_c)
     v_f, v_c, src = model(pr, seed)
-    rec = receivers(pr)
+    rec = receivers(pr, depths=TRACE_DEPTHS)
+    ng = rec.shape[0] // len(TRACE_DEPTHS)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     fs = fine_solver(pr, v_f, src, 2 * nt_c, rec)
     ev[0].record()
@@ -378,8 +385,12 @@ def evaluate(pr: Pairing, net, seed: int, nt_c: int, timing=False, closure_from=
         tr = cs.traces()
         cs.close()
         uu = u[phys].double()
+        by_depth = {}
+        for i, dep in enumerate(TRACE_DEPTHS):
+            sl = slice(i * ng, (i + 1) * ng)
+            by_depth[dep] = float(np.linalg.norm(tr[:, sl] - ref_tr[:, sl]) / np.linalg.norm(ref_tr[:, sl]))
         out[name] = {"field": float(torch.linalg.vector_norm(uu - ref_u) / torch.linalg.vector_norm(ref_u)),
-                     "traces": float(np.linalg.norm(tr - ref_tr) / np.linalg.norm(ref_tr))}
+                     "traces": by_depth[TRACE_DEPTHS[0]], "traces_by_depth": by_depth}
     if timing:
         out["ms"] = ms
     return out
