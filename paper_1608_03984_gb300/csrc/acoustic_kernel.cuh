@@ -19,6 +19,7 @@
 //   * z neighbours: a register queue of 2r + U planes per point; the z loop
 //     is unrolled U times so the queue shifts by U planes (2r moves) every U
 //     planes instead of every plane.
+// With RX even the point sums run on packed FP32 pairs (Pk<2> below).
 // TMA keeps NS stages in flight, each an mbarrier-tracked slot holding the
 // interior tile of plane z+r (queue head), and the halo tile, u_{n-1} tile
 // and c tile of output plane z. u_{n+1} goes straight from registers to
