@@ -211,12 +211,14 @@ def test_divergence_watchdog(fdw):
     s.close()
 
 
-def test_full_size_sampled_step(fdw, O):
-    """512^3 + 40-point sponge (592^3), order 8, the launch configuration of
-    the benchmark: one step from a random state, checked at sampled points
-    (interior, sponge, faces, corners) by the oracle's point update."""
+@pytest.mark.parametrize("order", [2, 4, 8, 12, 16])
+def test_full_size_sampled_step(fdw, O, order):
+    """512^3 + 40-point sponge (592^3), each order of the benchmark in its
+    launch configuration (default tile and z chunks): one step from a
+    random state, checked at sampled points (interior, sponge, faces,
+    corners) by the oracle's point update."""
     import torch
-    w = synth.random_acoustic(n=512, order=8, nt=8, nrec_side=16)
+    w = synth.random_acoustic(n=512, order=order, nt=8, nrec_side=16)
     s = fdw.Solver(w.n, w.h, w.nb, w.order)
     s.set_model(w.vp).set_dt(w.dt).set_receivers(w.rec_xyz, w.nt)
     comp = s.comp_shape
