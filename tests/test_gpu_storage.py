@@ -90,3 +90,50 @@ def test_field_scale_is_exact_bookkeeping(fdw):
         s.close()
     for a, b in zip(out[0], out[1]):
         assert rel(b, a) <= 1e-6
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("order", [4, 16])
+def test_full_size_sampled_step_16bit(fdw, O, storage, order):
+    """592^3 acoustic with 16-bit storage in the benchmark's launch
+    configuration: one step from a random state, checked at sampled points
+    against the FP64 point update of the stored (rounded) input levels. The
+    bound is one rounding of the stored output plus the rounding of the
+    stored medium, relative to the largest input of the stencil: |u+| and
+    c |lap u| stay below ~7 and ~4 times that maximum at CFL 0.4, so
+    2^-9 (BF16) or 2^-12 (FP16) times ~11 (tolerances below)."""
+    import torch
+    w = synth.random_acoustic(n=512, order=order, nt=8, nrec_side=16)
+    s = fdw.Solver(w.n, w.h, w.nb, w.order, storage=storage)
+    s.set_model(w.vp).set_dt(w.dt).set_receivers(w.rec_xyz, w.nt)
+    comp = s.comp_shape
+    g = torch.Generator(device="cuda").manual_seed(77 + order)
+    s.set_wavefield(1e-3 * torch.randn(comp, generator=g, device="cuda", dtype=torch.float32), 0, 0)
+    s.set_wavefield(1e-3 * torch.randn(comp, generator=g, device="cuda", dtype=torch.float32), 0, 1)
+    u = torch.empty(comp, device="cuda", dtype=torch.float32)
+    um = torch.empty_like(u)
+    s.wavefield(0, 0, out=u)   # the stored values, as the kernel reads them
+    s.wavefield(0, 1, out=um)
+    s.step(1)
+    up = torch.empty_like(u)
+    s.wavefield(0, 0, out=up)
+    s.check()
+    torch.cuda.synchronize()
+    r = order // 2
+    rng = np.random.default_rng(5)
+    N = np.array(comp)
+    pts = [tuple(int(v) for v in rng.integers(0, N)) for _ in range(40)]
+    pts += [(0, 0, 0), tuple(int(v) for v in N - 1), (39, 40, 41), (40, 40, 40), (591, 0, 295)]
+    gmax = O.sponge_gamma_max(float(w.vp.max()), w.nb, w.h)
+    prof = [O.sponge_profile(n, w.nb, gmax) for n in comp]
+    upad = torch.nn.functional.pad(u.view(1, 1, *comp), (r,) * 6)[0, 0]
+    worst = 0.0
+    for (k, j, i) in pts:
+        blk = upad[k:k + 2 * r + 1, j:j + 2 * r + 1, i:i + 2 * r + 1].double().cpu().numpy()
+        pk, pj, pi = (min(max(a - w.nb, 0), n - 1) for a, n in zip((k, j, i), w.n))
+        exp = O.acoustic_update_at(blk, float(um[k, j, i]), float(w.vp[pk, pj, pi]),
+                                   prof[0][k] + prof[1][j] + prof[2][i], w.h, order, w.dt)
+        worst = max(worst, abs(float(up[k, j, i]) - exp) / np.abs(blk).max())
+    tol = {"bf16": 2.5e-2, "f16": 3e-3}[storage]
+    assert worst < tol, worst
+    s.close()

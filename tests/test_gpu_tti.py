@@ -152,13 +152,14 @@ def test_every_tti_configuration(fdw, O, order, tile):
     s.close()
 
 
-def test_full_size_sampled_step(fdw, O):
-    """384^3 + 40-point sponge (464^3), order 8, the launch configuration of
-    the benchmark's TTI workload: one step from random p, r levels, checked
-    at sampled points (interior, sponge, faces, corners) by the oracle's TTI
-    point update with that point's medium."""
+@pytest.mark.parametrize("order", [8, 12])
+def test_full_size_sampled_step(fdw, O, order):
+    """384^3 + 40-point sponge (464^3), orders 8 and 12 in the launch
+    configuration of the benchmark's TTI workload: one step from random p,
+    r levels, checked at sampled points (interior, sponge, faces, corners)
+    by the oracle's TTI point update with that point's medium."""
     import torch
-    w = synth.random_tti(n=384, nb=40, order=8, nt=8, nrec_side=16)
+    w = synth.random_tti(n=384, nb=40, order=order, nt=8, nrec_side=16)
     s = tti_solver(fdw, w)
     comp = s.comp_shape
     g = torch.Generator(device="cuda").manual_seed(4321)
