@@ -41,7 +41,7 @@
 
 namespace fdw {
 
-template <typename T, int R, int BY, int NS, int U>
+template <typename T, int R, int BY, int NS, int U, bool SH = false>
 struct TtiTile {
   static constexpr int TX = 32;
   static constexpr int TY = BY;
@@ -57,7 +57,7 @@ struct TtiTile {
   static constexpr int N_INT = 9;
   static constexpr int STAGE_B = 2 * HALO_B + N_INT * INT_B;
   static constexpr int SY = TX + 2 * R;  // row length of the D_y scratch
-  static constexpr int SCR_B = a128(2 * 2 * TY * SY * 4);  // [buffer][field][TY][SY]
+  static constexpr int SCR_B = SH ? 0 : a128(2 * 2 * TY * SY * 4);  // [buffer][field][TY][SY]
   static constexpr int NHALO = 2 * 2 * R * TY;               // D_y halo items per plane
   static constexpr int HPW = (NHALO + BY - 1) / BY;          // items per warp
   static constexpr int BAR_B = 128;
@@ -70,9 +70,10 @@ struct TtiTile {
   static_assert((BXH * EL) % 16 == 0 && (TX * EL) % 16 == 0 && (HX * EL) % 16 == 0, "TMA alignment");
   static_assert(SMEM_B <= 227 * 1024, "shared memory per CTA");
   static_assert(HPW <= 32, "one D_y halo item per lane");
+  static_assert(2 * R <= 32, "shuffle variant: the row's D_y halo columns fit one warp");
 };
 
-template <typename T, int R, int BY, int NS, int U>
+template <typename T, int R, int BY, int NS, int U, bool SH>
 __global__ void __launch_bounds__(32 * BY)
     tti_tma_kernel(const __grid_constant__ CUtensorMap m_ph, const __grid_constant__ CUtensorMap m_rh,
                    const __grid_constant__ CUtensorMap m_pm, const __grid_constant__ CUtensorMap m_rm,
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(32 * BY)
                    const __grid_constant__ CUtensorMap m_d, const __grid_constant__ CUtensorMap m_ax,
                    const __grid_constant__ CUtensorMap m_ay, T *__restrict__ p_out,
                    T *__restrict__ r_out, Dims d, Weights w, Sponge sp, int zc, int *err) {
-  using C = TtiTile<T, R, BY, NS, U>;
+  using C = TtiTile<T, R, BY, NS, U, SH>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   float *scr = (float *)(smem + NS * C::STAGE_B);  // [2][2][TY][SY] D_y of p and r
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(32 * BY)
       // finish head plane j-1: D_x(D_y f) from scratch buffer (j-1)&1, then
       // its in-plane sums into the delay queue (slot R+u-1; for u = 0 that
       // is the previous group's last slot after the shift)
-      if (j >= 1) {
+      if (!SH && j >= 1) {
         float a0 = 0.f, a1 = 0.f;
         if (phead) {
           float A[2];
@@ -206,6 +207,13 @@ __global__ void __launch_bounds__(32 * BY)
       const bool head = (zh >= 0 && zh < d.NZ);
       float *sb = scr + (j & 1) * 2 * C::TY * C::SY;
       if (head) {
+        // shuffle variant: the head plane's axis and in-plane sums now
+        float hx = 0.f, hy = 0.f, Ash[2] = {0.f, 0.f};
+        if constexpr (SH) {
+          const T *HA = (const T *)(st + 2 * C::HALO_B);
+          hx = St<T>::ld(HA[li]);
+          hy = St<T>::ld(HA[C::INT_B / C::EL + li]);
+        }
 #pragma unroll
         for (int f = 0; f < 2; ++f) {
           const T *H = (const T *)(st + f * C::HALO_B);
@@ -226,11 +234,36 @@ __global__ void __launch_bounds__(32 * BY)
           q[3 * f + 0][2 * R + u] = fc;
           q[3 * f + 1][2 * R + u] = dx;
           q[3 * f + 2][2 * R + u] = dy;
-          sb[(f * C::TY + ty) * C::SY + R + tx] = dy;
+          if constexpr (SH) {
+            // D_x(D_y f) by warp shuffles: the warp is one row of 32
+            // points; lanes 0..R-1 also hold D_y f of the halo columns
+            // x = -R..-1 and lanes R..2R-1 those of x = 32..32+R-1
+            float dyh = 0.f;
+            if (tx < 2 * R) {
+              const int xo = tx < R ? tx - R : C::TX + (tx - R);
+              const T *col = H + (ty + R) * C::BXH + C::HX + xo;
+#pragma unroll
+              for (int m = 1; m <= R; ++m)
+                dyh = fmaf(w.c1[m], St<T>::ld(col[m * C::BXH]) - St<T>::ld(col[-m * C::BXH]), dyh);
+            }
+            float xy = 0.f;
+#pragma unroll
+            for (int m = 1; m <= R; ++m) {
+              const int xp = tx + m, xm = tx - m;
+              const float ap = __shfl_sync(0xffffffffu, dy, xp & 31);
+              const float bp = __shfl_sync(0xffffffffu, dyh, (R + xp - C::TX) & 31);
+              const float am = __shfl_sync(0xffffffffu, dy, xm & 31);
+              const float bm = __shfl_sync(0xffffffffu, dyh, (xm + R) & 31);
+              xy = fmaf(w.c1[m], (xp < C::TX ? ap : bp) - (xm >= 0 ? am : bm), xy);
+            }
+            Ash[f] = hx * hx * xx + hy * hy * yy + 2.f * hx * hy * xy;
+          } else {
+            sb[(f * C::TY + ty) * C::SY + R + tx] = dy;
+          }
         }
         // D_y of both fields in the x halo columns [-R, 0) and [32, 32 + R):
         // HPW items per warp, one per lane
-        if (tx < C::HPW) {
+        if (!SH && tx < C::HPW) {
           const int t = ty * C::HPW + tx;
           if (t < C::NHALO) {
             const int f = t / (2 * R * C::TY);
@@ -247,12 +280,21 @@ __global__ void __launch_bounds__(32 * BY)
             sb[(f * C::TY + yy_) * C::SY + R + xo] = dy;
           }
         }
-        const T *HA = (const T *)(st + 2 * C::HALO_B);
-        phx = St<T>::ld(HA[li]);
-        phy = St<T>::ld(HA[C::INT_B / C::EL + li]);
+        if constexpr (SH) {
+          dq[0][R + u] = pfxx[0] + pfyy[0] - Ash[0];
+          dq[1][R + u] = Ash[1];
+        } else {
+          const T *HA = (const T *)(st + 2 * C::HALO_B);
+          phx = St<T>::ld(HA[li]);
+          phy = St<T>::ld(HA[C::INT_B / C::EL + li]);
+        }
       } else {
 #pragma unroll
         for (int a = 0; a < 6; ++a) q[a][2 * R + u] = 0.f;
+        if constexpr (SH) {
+          dq[0][R + u] = 0.f;
+          dq[1][R + u] = 0.f;
+        }
       }
       phead = head;
       if (j < 2 * R) continue;
@@ -308,20 +350,25 @@ namespace fdw {
 
 constexpr int kTtiNS = 4;
 
-// Candidate configurations (warps per CTA = tile rows BY, z unrolling U),
-// selected at run time by index.
+// Candidate configurations (warps per CTA = tile rows BY, z unrolling U,
+// cross term through the shared D_y scratch (0) or warp shuffles (1)),
+// selected at run time by index. The shuffle form needs four shuffles per
+// tap (interior and halo lane, both sides) where the scratch needs two
+// shared loads, and measures 17-25% slower; it stays selectable.
 #define FDW_TTI_CFGS(X) \
-  X(0, 8, 2)            \
-  X(1, 4, 4)            \
-  X(2, 4, 2)            \
-  X(3, 2, 2)            \
-  X(4, 4, 1)
-constexpr int kTtiTiles = 5;
+  X(0, 8, 2, 0)         \
+  X(1, 4, 4, 0)         \
+  X(2, 4, 2, 0)         \
+  X(3, 2, 2, 0)         \
+  X(4, 4, 1, 0)         \
+  X(5, 4, 4, 1)         \
+  X(6, 4, 2, 1)
+constexpr int kTtiTiles = 7;
 
-template <typename T, int R, int BY, int U>
+template <typename T, int R, int BY, int U, int SH>
 cudaError_t launch_tti_cfg(const TTILaunch &L, cudaStream_t st) {
-  using C = TtiTile<T, R, BY, kTtiNS, U>;
-  auto kern = tti_tma_kernel<T, R, BY, kTtiNS, U>;
+  using C = TtiTile<T, R, BY, kTtiNS, U, SH != 0>;
+  auto kern = tti_tma_kernel<T, R, BY, kTtiNS, U, SH != 0>;
   if (L.prepare_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_B);
     if (e == cudaSuccess && L.occupancy_out)
@@ -339,9 +386,9 @@ cudaError_t launch_tti_cfg(const TTILaunch &L, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int R, int BY, int U>
+template <typename T, int R, int BY, int U, int SH>
 void tti_geom_cfg(TileGeom *g) {
-  using C = TtiTile<T, R, BY, kTtiNS, U>;
+  using C = TtiTile<T, R, BY, kTtiNS, U, SH != 0>;
   g->box_halo_x = C::BXH;
   g->box_halo_y = C::BYH;
   g->box_int_x = C::TX;
@@ -349,10 +396,10 @@ void tti_geom_cfg(TileGeom *g) {
   g->smem = C::SMEM_B;
 }
 
-#define FDW_TTI_CASE_LAUNCH(ID, BY, U) \
-  case ID: return launch_tti_cfg<TYPE_, R, BY, U>(L, st);
-#define FDW_TTI_CASE_GEOM(ID, BY, U) \
-  case ID: tti_geom_cfg<TYPE_, R, BY, U>(g); return 0;
+#define FDW_TTI_CASE_LAUNCH(ID, BY, U, SH) \
+  case ID: return launch_tti_cfg<TYPE_, R, BY, U, SH>(L, st);
+#define FDW_TTI_CASE_GEOM(ID, BY, U, SH) \
+  case ID: tti_geom_cfg<TYPE_, R, BY, U, SH>(g); return 0;
 
 #define FDW_TTI_DEFINE_STORAGE(SUFFIX, TYPE)                                  \
   template <typename TYPE_, int R>                                            \
