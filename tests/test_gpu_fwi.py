@@ -204,3 +204,50 @@ def test_misfit_matches_numpy_and_is_deterministic(fdw, n):
     assert abs(J1 - exp) <= 1e-12 * max(exp, 1e-300)
     with pytest.raises(ValueError):
         fdw.misfit(dt.float(), ot)
+
+
+def test_full_size_gradient(fdw):
+    """The benchmark's FWI workload (256^3 + 40-point sponge, order 8, 2000
+    steps) for two of its shots, in the benchmark's configuration: the
+    gradient with 20 checkpoints per shot equals the one with 13 (the
+    replays recompute the same forward states; only the order of the FP32
+    segment sums changes), and along two smooth model perturbations inside
+    the physical grid it matches Richardson-extrapolated central
+    differences of the misfit."""
+    import torch
+    from paper_1608_03984_gb300 import fwi
+    w = synth.fwi()
+    vref = 1.1 * float(max(w.v_true.max(), w.v_start.max()))
+
+    def survey(ck):
+        return fwi.Survey(w.n, w.h, w.nb, w.order, w.dt, w.nt, w.src_xyz[5:7], w.wavelet, w.rec_xyz,
+                          checkpoints=ck, sponge_vref=vref)
+
+    sv = survey(20)
+    with torch.no_grad():
+        d_obs = fwi.fwi_traces(torch.from_numpy(w.v_true).cuda(), sv)
+    v = torch.from_numpy(w.v_start).cuda()
+    J0, g = fwi.misfit_and_gradient(v, sv, d_obs)
+    J1, g1 = fwi.misfit_and_gradient(v, survey(13), d_obs)
+    assert torch.isfinite(g).all() and float(J0) > 0
+    assert abs(float(J1) - float(J0)) <= 1e-12 * float(J0)
+    assert float((g1 - g).double().norm() / g.double().norm()) <= 1e-5
+
+    def J(vv):
+        with torch.no_grad():
+            return float(0.5 * torch.sum((fwi.fwi_traces(vv, sv).double() - d_obs.double()) ** 2))
+
+    n = w.n[0]
+    for k in range(2):
+        dv = synth.smooth_random_field(w.n, 12, 2100 + k).astype(np.float64)
+        ramp = np.minimum(np.arange(n), np.arange(n)[::-1]).astype(np.float64)
+        ramp = np.clip(ramp / 16.0, 0.0, 1.0)  # zero at the faces of the physical grid
+        dv *= ramp[:, None, None] * ramp[None, :, None] * ramp[None, None, :]
+        dv *= 20.0 / np.abs(dv).max()
+        dvt = torch.from_numpy(dv.astype(np.float32)).cuda()
+        lin = float(torch.sum(g.double() * dvt.double()))
+        fd = {}
+        for eps in (0.5, 0.25):
+            fd[eps] = (J(v + eps * dvt) - J(v - eps * dvt)) / (2 * eps)
+        rich = (4 * fd[0.25] - fd[0.5]) / 3
+        assert abs(rich - lin) <= 3e-2 * abs(lin), (k, rich, lin)
