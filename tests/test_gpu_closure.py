@@ -345,3 +345,63 @@ def test_training_reduces_error_on_held_out_models(fdw):
     for key, v in ratios.items():
         assert np.mean(v) < 0.85, (key, v)
     net.close()
+
+
+def test_tensor_core_full_size_sampled(fdw, O):
+    """The benchmark's coarse grid (256^3 + 20-point sponge = 296^3, h = 20 m,
+    order 4) in the launch configuration of its closure runs (tensor-core
+    inference, default chunking): one closure step from random levels. At
+    sampled points the correction (closure step minus plain step) matches
+    the oracle's net(x) - net(x0) on the 7^3 block around the point, times
+    m = max |u_n|; in the sponge and its 3-point margin it is exactly zero.
+    Bound: FP16 rounding of the activations, as in the small-grid test."""
+    import torch
+    from paper_1608_03984_gb300 import synth
+    n, nb, h, order = 256, 20, 20.0, 4
+    vp = synth.random_velocity((n, n, n), h, 200.0, 91)
+    dt = 0.35 * h / 4500.0
+    p = random_params(92, scale=0.3)
+    runs = []
+    for closure in (True, False):
+        s = fdw.Solver(vp.shape, h, nb, order)
+        s.set_model(vp).set_sponge(4500.0).set_dt(dt)
+        comp = s.comp_shape
+        g = torch.Generator(device="cuda").manual_seed(93)
+        u = torch.randn(comp, generator=g, device="cuda", dtype=torch.float32)
+        um = torch.randn(comp, generator=g, device="cuda", dtype=torch.float32)
+        s.set_wavefield(u, 0, 0)
+        s.set_wavefield(um, 0, 1)
+        if closure:
+            net = fdw.Closure()
+            net.set_params(p)
+            s.step_closure(net, 1)
+            net.close()
+        else:
+            s.step(1)
+        out = torch.empty_like(u)
+        s.wavefield(0, 0, out=out)
+        s.check()
+        s.close()
+        runs.append(out)
+    corr = (runs[0].double() - runs[1].double()).cpu().numpy()
+    u, um = u.double().cpu().numpy(), um.double().cpu().numpy()
+    m = float(np.abs(u).max())
+    vn = (O.extend(vp, nb) - 3000.0) / 750.0
+    N = comp[0]
+    a = nb + 3
+    rng = np.random.default_rng(94)
+    pts = [tuple(int(v) for v in rng.integers(a, N - a, size=3)) for _ in range(40)]
+    pts += [(a, a, a), (N - a - 1,) * 3, (a, N // 2, N - a - 1), (N // 2,) * 3]
+    got, ref = [], []
+    for (k, j, i) in pts:
+        sl = (slice(k - 3, k + 4), slice(j - 3, j + 4), slice(i - 3, i + 4))
+        x = np.stack([u[sl] / m, um[sl] / m, vn[sl]])
+        ref.append(m * float(O.closure_correction(p.astype(np.float64), x)[0, 0, 0]))
+        got.append(corr[k, j, i])
+    got, ref = np.array(got), np.array(ref)
+    assert np.abs(ref).max() > 0
+    assert np.abs(got - ref).max() <= 1e-2 * np.abs(ref).max(), np.abs(got - ref).max() / np.abs(ref).max()
+    # no correction in the sponge and its margin
+    band = np.ones(comp, bool)
+    band[a:N - a, a:N - a, a:N - a] = False
+    assert np.all(corr[band] == 0.0)
