@@ -209,7 +209,7 @@ int fdw_set_zchunks(fdw_solver *s, int zchunks);
 /*
  * Tile configuration of the 2.5D kernel: acoustic (points per thread in x/y,
  * warps per CTA, z unrolling; acoustic_kernel.cuh) or TTI (warps per CTA, z
- * unrolling; tti_kernel.cuh): acoustic 0..5, TTI 0..6, or -1 for the
+ * unrolling; tti_kernel.cuh): acoustic 0..5, TTI 0..8, or -1 for the
  * default of the solver's equation, order and storage. Resets zchunks to
  * its default.
  * fdw_get_tile_config returns the configuration in use (-1 for NULL).

@@ -502,6 +502,8 @@ extern "C" int fdw_create(fdw_solver **out, int nx, int ny, int nz, double h, in
       s->w.w2[j] = j <= s->r ? (float)w2[j] : 0.f;
       s->w.c1[j] = j <= s->r ? (float)c1[j] : 0.f;
       s->w.w2p[j] = make_float2(s->w.w2[j], s->w.w2[j]);
+      s->w.c1p[j] = make_float2(s->w.c1[j], s->w.c1[j]);
+      s->w.c1n[j] = make_float2(-s->w.c1[j], -s->w.c1[j]);
     }
   }
   int rc = FDW_OK;

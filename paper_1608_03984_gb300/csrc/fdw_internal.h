@@ -34,6 +34,8 @@ struct Weights {
   float w2[kMaxR + 1];    // second derivative
   float c1[kMaxR + 1];    // first derivative (c1[0] = 0)
   float2 w2p[kMaxR + 1];  // w2 as pairs {w2, w2}, for packed FP32 arithmetic
+  float2 c1p[kMaxR + 1];  // c1 as pairs {c1, c1}
+  float2 c1n[kMaxR + 1];  // -c1 as pairs
 };
 
 // Damping tables: gh_a[i] = gamma_a(i) * dt / 2 for each axis.
@@ -128,7 +130,7 @@ struct TTILaunch {
   // level n-1 and of the medium fields
   const CUtensorMap *m_ph, *m_rh, *m_pm, *m_rm, *m_c, *m_e, *m_d, *m_ax, *m_ay;
 };
-constexpr int kTtiTilesMax = 7;  // number of TTI configurations (see tti_kernel.cuh)
+constexpr int kTtiTilesMax = 9;  // number of TTI configurations (see tti_kernel.cuh)
 cudaError_t launch_tti(const TTILaunch &L, cudaStream_t st);
 cudaError_t tti_prepare(int storage, int r, int tile);
 int tti_geom(int storage, int r, int tile, TileGeom *g);

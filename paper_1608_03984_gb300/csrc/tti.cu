@@ -126,12 +126,14 @@ int tti_geom(int storage, int r, int tile, TileGeom *g) {
   }
 }
 
-// Default configuration: four warps per CTA (measured on the 464^3 TTI
-// workload: 4 warps beat 2 and 8), z unrolling 4 up to order 8, 2 at
-// orders 10-12, 1 above (the queues of 6 fields grow with the order).
+// Default configuration (measured on the 464^3 TTI workload): four warps
+// per CTA (they beat 2 and 8); up to order 8 the field-pair kernel (z
+// unrolling 4 for FP32, 1 for 16-bit storage), above it the scalar one
+// with z unrolling 2 at orders 10-12 and 1 higher (the queues of 6 fields
+// grow with the order and the pairs' extra registers cost occupancy).
 int tti_default_tile(int storage, int r) {
-  (void)storage;
-  return r <= 4 ? 1 : r <= 6 ? 2 : 4;
+  if (r <= 4) return storage == FDW_F32 ? 7 : 8;
+  return r <= 6 ? 2 : 4;
 }
 
 int tti_ctas_per_sm(int storage, int r, int tile) {

@@ -344,6 +344,243 @@ __global__ void __launch_bounds__(32 * BY)
   }
 }
 
+// Field-pair variant of the kernel above (scratch cross term): p and r go
+// through the same stencils with the same weights, so their arithmetic runs
+// on (p, r) pairs with f32x2 instructions (__ffma2_rn, __fadd2_rn,
+// __fmul2_rn; per component the scalar rounding), a difference a - b taken
+// as c1 a + (-c1) b. Fewer issue slots, more registers: faster at orders up
+// to 8, slower above (occupancy).
+template <typename T, int R, int BY, int NS, int U>
+__global__ void __launch_bounds__(32 * BY)
+    tti_tma_pk_kernel(const __grid_constant__ CUtensorMap m_ph, const __grid_constant__ CUtensorMap m_rh,
+                      const __grid_constant__ CUtensorMap m_pm, const __grid_constant__ CUtensorMap m_rm,
+                      const __grid_constant__ CUtensorMap m_c, const __grid_constant__ CUtensorMap m_e,
+                      const __grid_constant__ CUtensorMap m_d, const __grid_constant__ CUtensorMap m_ax,
+                      const __grid_constant__ CUtensorMap m_ay, T *__restrict__ p_out,
+                      T *__restrict__ r_out, Dims d, Weights w, Sponge sp, int zc, int *err) {
+  using C = TtiTile<T, R, BY, NS, U, false>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  float *scr = (float *)(smem + NS * C::STAGE_B);  // [2][2][TY][SY] D_y of p and r
+  uint64_t *bars = (uint64_t *)(smem + NS * C::STAGE_B + C::SCR_B);
+  float *gzs = (float *)(smem + NS * C::STAGE_B + C::SCR_B + C::BAR_B);
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + tx;
+  const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, d.NZ);
+  if (z0 >= z1 || zc > kMaxZChunk) return;  // uniform over the CTA
+  const int nit = (z1 - z0) + 2 * R;
+  const float gxr = (x0 + tx < d.NX) ? sp.gx[x0 + tx] : 0.f;
+  const float gyr = (y0 + ty < d.NY) ? sp.gy[y0 + ty] : 0.f;
+
+  const CUtensorMap *maps_int[C::N_INT] = {&m_ax, &m_ay, &m_pm, &m_rm, &m_c, &m_e, &m_d, &m_ax, &m_ay};
+  if (tid == 0) {
+    prefetch_tensormap(&m_ph);
+    prefetch_tensormap(&m_rh);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) prefetch_tensormap(maps_int[2 + i]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    fence_barrier_init();
+  }
+  for (int i = tid; i < z1 - z0; i += C::THREADS) gzs[i] = sp.gz[z0 + i];
+  __syncthreads();
+
+  int issued_hi = -1;
+  auto issue = [&](int j) {
+    const int s = j % NS;
+    const int zh = z0 - R + j;
+    const bool head = (zh >= 0 && zh < d.NZ);
+    const bool outp = (j >= 2 * R);
+    const uint32_t bytes = (head ? (2 * C::BXH * C::BYH + 2 * C::TX * C::TY) * C::EL : 0) +
+                           (outp ? 7 * C::TX * C::TY * C::EL : 0);
+    const uint32_t bar = smem_u32(&bars[s]);
+    unsigned char *st = smem + s * C::STAGE_B;
+    mbar_arrive_expect_tx(bar, bytes);
+    if (head) {
+      tma_load_3d(smem_u32(st), &m_ph, x0 - C::HX, y0 - R, zh, bar);
+      tma_load_3d(smem_u32(st + C::HALO_B), &m_rh, x0 - C::HX, y0 - R, zh, bar);
+      tma_load_3d(smem_u32(st + 2 * C::HALO_B + 0 * C::INT_B), &m_ax, x0, y0, zh, bar);
+      tma_load_3d(smem_u32(st + 2 * C::HALO_B + 1 * C::INT_B), &m_ay, x0, y0, zh, bar);
+    }
+    if (outp) {
+      const int zo = zh - R;
+#pragma unroll
+      for (int i = 2; i < C::N_INT; ++i)
+        tma_load_3d(smem_u32(st + 2 * C::HALO_B + i * C::INT_B), maps_int[i], x0, y0, zo, bar);
+    }
+    issued_hi = j;
+  };
+  if (tid == 0) {
+    const int n0 = nit < NS ? nit : NS;
+    for (int j = 0; j < n0; ++j) issue(j);
+  }
+
+  // The two fields go through the same stencils with the same weights, so
+  // the arithmetic runs on (p, r) pairs with f32x2 instructions
+  // (__ffma2_rn, __fadd2_rn, __fmul2_rn; per component the scalar
+  // rounding); a difference a - b is taken as c1 a + (-c1) b.
+  // queues of (p, r) pairs: [0] f, [1] D_x f, [2] D_y f
+  float2 q[3][C::QL];
+  float2 dq[C::DL];  // delayed in-plane sums (p_xx + p_yy - A p, A r)
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int i = 0; i < C::QL; ++i) q[a][i] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < C::DL; ++i) dq[i] = make_float2(0.f, 0.f);
+
+  const size_t plane = d.plane();
+  const int li = ty * C::TX + tx;  // index inside an interior tile
+  // in-plane second derivatives and axis of the previous head plane, whose
+  // cross term is finished one iteration later
+  float2 pfxx = make_float2(0.f, 0.f), pfyy = make_float2(0.f, 0.f);
+  float phx = 0.f, phy = 0.f;
+  bool phead = false;
+  // A f = nx^2 f_xx + ny^2 f_yy + 2 nx ny f_xy for both fields, and the
+  // in-plane sums (f_xx + f_yy - A f for p, A f for r)
+  auto inplane = [&](float hx, float hy, float2 fxx, float2 fyy, float2 fxy) {
+    const float2 A = __ffma2_rn(make_float2(2.f * hx * hy, 2.f * hx * hy), fxy,
+                                __ffma2_rn(make_float2(hy * hy, hy * hy), fyy,
+                                           __fmul2_rn(make_float2(hx * hx, hx * hx), fxx)));
+    return make_float2(fxx.x + fyy.x - A.x, A.y);
+  };
+
+#pragma unroll 1
+  for (int j0 = 0; j0 < nit; j0 += U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + u;
+      if (j >= nit) break;  // uniform
+      const int s = j % NS;
+      const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((j / NS) & 1));
+      // Also the point where every thread has finished iteration j-1 (its
+      // stage reads and its D_y scratch writes).
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(err, kErrWaitTimeout);
+          for (int jj = j; jj <= issued_hi; ++jj)
+            (void)mbar_wait_bounded(smem_u32(&bars[jj % NS]), (uint32_t)((jj / NS) & 1));
+        }
+        return;
+      }
+      if (tid == 0 && j >= 1 && j - 1 + NS < nit) issue(j - 1 + NS);
+
+      // finish head plane j-1: D_x(D_y f) from scratch buffer (j-1)&1, then
+      // its in-plane sums into the delay queue (slot R+u-1; for u = 0 that
+      // is the previous group's last slot after the shift)
+      if (j >= 1) {
+        float2 a = make_float2(0.f, 0.f);
+        if (phead) {
+          const float *sr0 = scr + (((j - 1) & 1) * 2 * C::TY + ty) * C::SY + R + tx;
+          const float *sr1 = sr0 + C::TY * C::SY;
+          float2 xy = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int m = 1; m <= R; ++m) {
+            xy = __ffma2_rn(w.c1p[m], make_float2(sr0[m], sr1[m]), xy);
+            xy = __ffma2_rn(w.c1n[m], make_float2(sr0[-m], sr1[-m]), xy);
+          }
+          a = inplane(phx, phy, pfxx, pfyy, xy);
+        }
+        dq[R + u - 1] = a;
+      }
+
+      const unsigned char *st = smem + s * C::STAGE_B;
+      const int zh = z0 - R + j;
+      const bool head = (zh >= 0 && zh < d.NZ);
+      float *sb = scr + (j & 1) * 2 * C::TY * C::SY;
+      if (head) {
+        const T *Hp = (const T *)st;
+        const T *Hr = (const T *)(st + C::HALO_B);
+        const int o0 = (ty + R) * C::BXH + C::HX + tx;
+        auto pr = [&](int o) { return make_float2(St<T>::ld(Hp[o]), St<T>::ld(Hr[o])); };
+        const float2 fc = pr(o0);
+        float2 xx = __fmul2_rn(w.w2p[0], fc), yy = xx, dx = make_float2(0.f, 0.f), dy = dx;
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+          const float2 xp = pr(o0 + m), xm = pr(o0 - m);
+          const float2 yp = pr(o0 + m * C::BXH), ym = pr(o0 - m * C::BXH);
+          xx = __ffma2_rn(w.w2p[m], __fadd2_rn(xp, xm), xx);
+          dx = __ffma2_rn(w.c1n[m], xm, __ffma2_rn(w.c1p[m], xp, dx));
+          yy = __ffma2_rn(w.w2p[m], __fadd2_rn(yp, ym), yy);
+          dy = __ffma2_rn(w.c1n[m], ym, __ffma2_rn(w.c1p[m], yp, dy));
+        }
+        pfxx = xx;
+        pfyy = yy;
+        q[0][2 * R + u] = fc;
+        q[1][2 * R + u] = dx;
+        q[2][2 * R + u] = dy;
+        {
+          sb[ty * C::SY + R + tx] = dy.x;
+          sb[(C::TY + ty) * C::SY + R + tx] = dy.y;
+          // D_y of both fields in the x halo columns [-R, 0) and
+          // [32, 32 + R): HPW items per warp, one per lane
+          if (tx < C::HPW) {
+            const int t = ty * C::HPW + tx;
+            if (t < C::NHALO) {
+              const int f = t / (2 * R * C::TY);
+              const int rem = t - f * (2 * R * C::TY);
+              const int yy_ = rem / (2 * R);
+              const int k = rem - yy_ * (2 * R);
+              const int xo = k < R ? k - R : C::TX + (k - R);  // tile x of the halo column
+              const T *H = (const T *)(st + f * C::HALO_B);
+              const T *col = H + (yy_ + R) * C::BXH + C::HX + xo;
+              float dyh = 0.f;
+#pragma unroll
+              for (int m = 1; m <= R; ++m)
+                dyh = fmaf(w.c1[m], St<T>::ld(col[m * C::BXH]) - St<T>::ld(col[-m * C::BXH]), dyh);
+              sb[(f * C::TY + yy_) * C::SY + R + xo] = dyh;
+            }
+          }
+          const T *HA = (const T *)(st + 2 * C::HALO_B);
+          phx = St<T>::ld(HA[li]);
+          phy = St<T>::ld(HA[C::INT_B / C::EL + li]);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) q[a][2 * R + u] = make_float2(0.f, 0.f);
+      }
+      phead = head;
+      if (j < 2 * R) continue;
+
+      // output plane zo = zh - R
+      const int zo = zh - R;
+      const T *O = (const T *)(st + 2 * C::HALO_B);
+      auto tileval = [&](int i) { return St<T>::ld(O[i * (C::INT_B / C::EL) + li]); };
+      const float pm = tileval(2), rm = tileval(3), cc = tileval(4), ee = tileval(5), dd = tileval(6);
+      const float nx = tileval(7), ny = tileval(8);
+      const float nz = sqrtf(fmaxf(0.f, 1.f - nx * nx - ny * ny));
+      float2 zz = __fmul2_rn(w.w2p[0], q[0][u + R]), xz = make_float2(0.f, 0.f), yz = xz;
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        zz = __ffma2_rn(w.w2p[m], __fadd2_rn(q[0][u + R + m], q[0][u + R - m]), zz);
+        xz = __ffma2_rn(w.c1n[m], q[1][u + R - m], __ffma2_rn(w.c1p[m], q[1][u + R + m], xz));
+        yz = __ffma2_rn(w.c1n[m], q[2][u + R - m], __ffma2_rn(w.c1p[m], q[2][u + R + m], yz));
+      }
+      const float Hp = dq[u].x + (1.f - nz * nz) * zz.x - 2.f * nz * (nx * xz.x + ny * yz.x);
+      const float Gr = dq[u].y + nz * nz * zz.y + 2.f * nz * (nx * xz.y + ny * yz.y);
+      const float gh = gxr + gyr + gzs[zo - z0];
+      const float inv = __fdividef(1.f, 1.f + gh), qq = 1.f - gh;
+      const float pn = (2.f * q[0][u + R].x - qq * pm + cc * (ee * Hp + dd * Gr)) * inv;
+      const float rn = (2.f * q[0][u + R].y - qq * rm + cc * (dd * Hp + Gr)) * inv;
+      const int x = x0 + tx, y = y0 + ty;
+      if (x < d.NX && y < d.NY) {
+        const size_t o = (size_t)zo * plane + (size_t)y * d.Xp + x;
+        p_out[o] = St<T>::st(pn);
+        r_out[o] = St<T>::st(rn);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int i = 0; i < 2 * R; ++i) q[a][i] = q[a][i + U];
+#pragma unroll
+    for (int i = 0; i < R; ++i) dq[i] = dq[i + U];
+  }
+}
+
 }  // namespace fdw
 
 namespace fdw {
@@ -351,8 +588,9 @@ namespace fdw {
 constexpr int kTtiNS = 4;
 
 // Candidate configurations (warps per CTA = tile rows BY, z unrolling U,
-// cross term through the shared D_y scratch (0) or warp shuffles (1)),
-// selected at run time by index. The shuffle form needs four shuffles per
+// variant: 0 scalar with the cross term through the shared D_y scratch,
+// 1 scalar with warp shuffles, 2 field pairs with the scratch), selected at
+// run time by index. The shuffle form needs four shuffles per
 // tap (interior and halo lane, both sides) where the scratch needs two
 // shared loads, and measures 17-25% slower; it stays selectable.
 #define FDW_TTI_CFGS(X) \
@@ -362,13 +600,20 @@ constexpr int kTtiNS = 4;
   X(3, 2, 2, 0)         \
   X(4, 4, 1, 0)         \
   X(5, 4, 4, 1)         \
-  X(6, 4, 2, 1)
-constexpr int kTtiTiles = 7;
+  X(6, 4, 2, 1)         \
+  X(7, 4, 4, 2)         \
+  X(8, 4, 1, 2)
+constexpr int kTtiTiles = 9;
 
-template <typename T, int R, int BY, int U, int SH>
+template <typename T, int R, int BY, int U, int V>
 cudaError_t launch_tti_cfg(const TTILaunch &L, cudaStream_t st) {
-  using C = TtiTile<T, R, BY, kTtiNS, U, SH != 0>;
-  auto kern = tti_tma_kernel<T, R, BY, kTtiNS, U, SH != 0>;
+  using C = TtiTile<T, R, BY, kTtiNS, U, V == 1>;
+  auto kern = [] {
+    if constexpr (V == 2)
+      return tti_tma_pk_kernel<T, R, BY, kTtiNS, U>;
+    else
+      return tti_tma_kernel<T, R, BY, kTtiNS, U, V == 1>;
+  }();
   if (L.prepare_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_B);
     if (e == cudaSuccess && L.occupancy_out)
@@ -386,9 +631,9 @@ cudaError_t launch_tti_cfg(const TTILaunch &L, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int R, int BY, int U, int SH>
+template <typename T, int R, int BY, int U, int V>
 void tti_geom_cfg(TileGeom *g) {
-  using C = TtiTile<T, R, BY, kTtiNS, U, SH != 0>;
+  using C = TtiTile<T, R, BY, kTtiNS, U, V == 1>;
   g->box_halo_x = C::BXH;
   g->box_halo_y = C::BYH;
   g->box_int_x = C::TX;
@@ -396,10 +641,10 @@ void tti_geom_cfg(TileGeom *g) {
   g->smem = C::SMEM_B;
 }
 
-#define FDW_TTI_CASE_LAUNCH(ID, BY, U, SH) \
-  case ID: return launch_tti_cfg<TYPE_, R, BY, U, SH>(L, st);
-#define FDW_TTI_CASE_GEOM(ID, BY, U, SH) \
-  case ID: tti_geom_cfg<TYPE_, R, BY, U, SH>(g); return 0;
+#define FDW_TTI_CASE_LAUNCH(ID, BY, U, V) \
+  case ID: return launch_tti_cfg<TYPE_, R, BY, U, V>(L, st);
+#define FDW_TTI_CASE_GEOM(ID, BY, U, V) \
+  case ID: tti_geom_cfg<TYPE_, R, BY, U, V>(g); return 0;
 
 #define FDW_TTI_DEFINE_STORAGE(SUFFIX, TYPE)                                  \
   template <typename TYPE_, int R>                                            \

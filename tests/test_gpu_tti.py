@@ -128,7 +128,7 @@ def test_vti_matches_oracle(fdw, O):
 
 
 @pytest.mark.parametrize("order", [2, 8, 12, 16])
-@pytest.mark.parametrize("tile", list(range(7)))
+@pytest.mark.parametrize("tile", list(range(9)))
 def test_every_tti_configuration(fdw, O, order, tile):
     """Each (warps per CTA, z unrolling) configuration of the TTI kernel
     reproduces the oracle's step (ragged tile tails in x, y and z), and
