@@ -7,6 +7,13 @@ the paper's order and notation), this module marshals numpy arrays and holds
 the set-up steps the paper states as formulas (CFL limit of Eq. stability,
 the sponge-medium extension, c = dt^2 v^2).
 
+Parity unpinned (conventions the paper does not fix; nothing outside the
+oracle fixes their values, so only the GPU-vs-oracle parity covers them):
+the sponge constants of ``sponge_gamma_max`` / ``sponge_profile`` (reflection
+coefficient R = 1e-3, linear ramp; the tests only pin that the sponge
+absorbs), the medium extension into the sponge of ``extend`` (edge values),
+and the receiver sampling of the forward runs (nt + 1 samples, d[0] = 0).
+
 Array convention: numpy arrays of shape (nz, ny, nx), C order, x fastest.
 Positions are (x, y, z) metres of the physical grid, whose first point is at
 the origin; the computational grid adds ``nb`` sponge points on every face.
