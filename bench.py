@@ -560,6 +560,9 @@ def run_fwi(args):
             "gradient_finite": bool(torch.isfinite(g).all())}
 
 
+EVERIES = (1, 2, 4, 8, 16)  # closure on every e-th step (correction times e)
+
+
 def run_closure(args):
     """The learned closure: fine order 16 at h = 10 m vs coarse order 4 at
     h = 20 m (coarse point i = fine point 2i, dt_c = 2 dt_f), 10 Hz Ricker
@@ -597,9 +600,21 @@ def run_closure(args):
     nt = pr.steps_to_cross(0.45)
     evals = []
     for seed in range(5064, 5064 + args.closure_eval):
-        evals.append(C.evaluate(pr, net, seed, nt, timing=True))
+        evals.append(C.evaluate(pr, net, seed, nt, timing=True, everies=EVERIES))
     net.close()
-    ms = {k: float(np.mean([r["ms"][k] for r in evals])) for k in ("fine", "coarse", "closure")}
+    ms = {k: float(np.mean([r["ms"][k] for r in evals])) for k in evals[0]["ms"]}
+    # the closure on every e-th step with the correction times e: 1/e of the
+    # network's cost per unit of time
+    sub = {}
+    for e in EVERIES[1:]:
+        key = "closure_every%d" % e
+        sub[str(e)] = {
+            "error_vs_fine": {k: float(np.mean([r[key][k] for r in evals])) for k in ("field", "traces")},
+            "models_improved": {k: int(sum(r[key][k] < r["coarse"][k] for r in evals)) for k in ("field", "traces")},
+            "median_error_ratio": {k: float(np.median([r[key][k] / r["coarse"][k] for r in evals]))
+                                   for k in ("field", "traces")},
+            "traces_400m": float(np.mean([r[key]["traces_by_depth"][20] for r in evals])),
+            "ms": ms[key], "speedup_vs_fine": ms["fine"] / ms[key]}
     err = {m: {k: float(np.mean([r[m][k] for r in evals])) for k in ("field", "traces")}
            for m in ("coarse", "closure")}
     better = {k: int(sum(r["closure"][k] < r["coarse"][k] for r in evals)) for k in ("field", "traces")}
@@ -628,7 +643,8 @@ def run_closure(args):
             "inference": "tensor cores (mma.sync m16n8k16, FP16 operands, FP32 accumulation)",
             "one_step_unexplained": unexpl, "train_loss_first_last": [losses[0], losses[-1]],
             "data_s": t1 - t0, "train_s": t2 - t1, "iters": args.closure_iters,
-            "per_model": [{"coarse": r["coarse"], "closure": r["closure"]} for r in evals]}
+            "every_k_steps": sub,
+            "per_model": [{k: v for k, v in r.items() if k != "ms"} for r in evals]}
 
 
 def run_e2e(args, orders, base, stream):

@@ -393,6 +393,15 @@ int fdw_closure_adam_step(fdw_closure *c, const float *x, const float *target, i
 int fdw_step_closure(fdw_solver *s, fdw_closure *c, int nsteps);
 
 /*
+ * fdw_step_closure with the correction applied only on every `every`-th
+ * step of the call (steps 0, every, 2 every, ...; the others are plain
+ * steps) and multiplied by `every` there, so that the correction per unit
+ * of time stays the same at 1/every of the network's cost. every = 1 is
+ * fdw_step_closure. Errors: as fdw_step_closure; INVALID_ARG for every < 1.
+ */
+int fdw_step_closure_every(fdw_solver *s, fdw_closure *c, int nsteps, int every);
+
+/*
  * Kernel timing. After fdw_profile_begin, up to max_launches (<= 65536)
  * stencil launches issued by fdw_step are bracketed by CUDA events recorded
  * on the solver's stream (steps are then launched individually instead of

@@ -341,14 +341,16 @@ def receivers(pr: Pairing, nside=8, depths=(5,)):
                            for dep in depths])
 
 
-def evaluate(pr: Pairing, net, seed: int, nt_c: int, timing=False, closure_from=None):
+def evaluate(pr: Pairing, net, seed: int, nt_c: int, timing=False, closure_from=None, everies=(1,)):
     """Relative L2 errors of the coarse run alone and with the closure
     against the restricted fine run: final level (physical part) and traces
     (receivers of `receivers` at 5 coarse spacings depth, fine traces at
     the coarse times; `traces_by_depth` repeats it for every depth of
     TRACE_DEPTHS). The closure run takes plain steps until `closure_from`
     (default: the end of the source, pr.source_steps()), then closure
-    steps. With timing=True also the device milliseconds of each run."""
+    steps: on every step ("closure"), or on every e-th step with the
+    correction times e ("closure_every<e>") for each e of `everies`. With
+    timing=True also the device milliseconds of each run."""
     k1 = pr.source_steps() if closure_from is None else int(closure_from)
     k1 = min(max(k1, 0), nt_c)
     v_f, v_c, src = model(pr, seed)
@@ -369,7 +371,8 @@ def evaluate(pr: Pairing, net, seed: int, nt_c: int, timing=False, closure_from=
     ref_u = restrict(full)[phys].double()
     fs.close()
     out = {}
-    for name in ("coarse", "closure"):
+    runs = [("coarse", 0)] + [("closure" if e == 1 else "closure_every%d" % e, e) for e in everies]
+    for name, every in runs:
         cs = coarse_solver(pr, v_c, src, nt_c, rec)
         u = torch.empty(cs.comp_shape, dtype=torch.float32, device="cuda")
         ev[0].record()
@@ -377,7 +380,7 @@ def evaluate(pr: Pairing, net, seed: int, nt_c: int, timing=False, closure_from=
             cs.step(nt_c)
         else:
             cs.step(k1)
-            cs.step_closure(net, nt_c - k1)
+            cs.step_closure(net, nt_c - k1, every=every)
         ev[1].record()
         torch.cuda.synchronize()
         ms[name] = ev[0].elapsed_time(ev[1])

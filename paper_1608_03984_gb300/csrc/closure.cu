@@ -361,11 +361,11 @@ __global__ void __launch_bounds__(256)
     closure_apply_kernel(const float *__restrict__ a2, const __nv_bfloat16 *__restrict__ w3,
                          const float *__restrict__ b3, const float *__restrict__ base,
                          const float *__restrict__ s_dev, T *__restrict__ u, Dims d, int nb, int nx,
-                         int ny, int nz) {
+                         int ny, int nz, float factor) {
   __shared__ float ws[kH * 27];
   for (int i = threadIdx.x; i < kH * 27; i += blockDim.x) ws[i] = __bfloat162float(w3[i]);
   __syncthreads();
-  const float s = *s_dev;
+  const float s = factor * *s_dev;
   const long long vol = (long long)d.NX * d.NY * d.NZ;
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < vol;
        q += (long long)gridDim.x * blockDim.x) {
@@ -509,8 +509,8 @@ cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const v
 template <typename T>
 __global__ void closure_apply_out_kernel(const float *__restrict__ net, const float *__restrict__ base,
                                          const float *__restrict__ s_dev, T *__restrict__ u, Dims d, int nb,
-                                         int nx, int ny, int nz) {
-  const float s = *s_dev;
+                                         int nx, int ny, int nz, float factor) {
+  const float s = factor * *s_dev;
   // rows (j, k) whose points can be corrected; one block per row
   const int y0 = nb + kHalo, y1 = nb + ny - kHalo, z0 = nb + kHalo, z1 = nb + nz - kHalo;
   const int x0 = nb + kHalo, x1 = nb + nx - kHalo;
@@ -525,21 +525,21 @@ __global__ void closure_apply_out_kernel(const float *__restrict__ net, const fl
 }
 
 cudaError_t closure_infer_apply(ClosureNet *c, int storage, void *unew, Dims d, int nx, int ny, int nz, int nb,
-                                cudaStream_t st) {
+                                float factor, cudaStream_t st) {
   const long long vol = (long long)d.NX * d.NY * d.NZ;
   if (c->variant == 0) {
     switch (storage) {
       case FDW_F32:
         closure_apply_out_kernel<float><<<grid_for(vol), 256, 0, st>>>(c->tc_out, c->base, c->s_dev, (float *)unew,
-                                                                       d, nb, nx, ny, nz);
+                                                                       d, nb, nx, ny, nz, factor);
         break;
       case FDW_BF16:
         closure_apply_out_kernel<__nv_bfloat16><<<grid_for(vol), 256, 0, st>>>(
-            c->tc_out, c->base, c->s_dev, (__nv_bfloat16 *)unew, d, nb, nx, ny, nz);
+            c->tc_out, c->base, c->s_dev, (__nv_bfloat16 *)unew, d, nb, nx, ny, nz, factor);
         break;
       case FDW_F16:
         closure_apply_out_kernel<__half><<<grid_for(vol), 256, 0, st>>>(c->tc_out, c->base, c->s_dev,
-                                                                        (__half *)unew, d, nb, nx, ny, nz);
+                                                                        (__half *)unew, d, nb, nx, ny, nz, factor);
         break;
       default: return cudaErrorInvalidValue;
     }
@@ -548,15 +548,15 @@ cudaError_t closure_infer_apply(ClosureNet *c, int storage, void *unew, Dims d, 
   switch (storage) {
     case FDW_F32:
       closure_apply_kernel<float><<<grid_for(vol), 256, 0, st>>>(c->ia2, c->pb + kOffW3, c->pf + kOffB3, c->base, c->s_dev,
-                                                                 (float *)unew, d, nb, nx, ny, nz);
+                                                                 (float *)unew, d, nb, nx, ny, nz, factor);
       break;
     case FDW_BF16:
       closure_apply_kernel<__nv_bfloat16><<<grid_for(vol), 256, 0, st>>>(
-          c->ia2, c->pb + kOffW3, c->pf + kOffB3, c->base, c->s_dev, (__nv_bfloat16 *)unew, d, nb, nx, ny, nz);
+          c->ia2, c->pb + kOffW3, c->pf + kOffB3, c->base, c->s_dev, (__nv_bfloat16 *)unew, d, nb, nx, ny, nz, factor);
       break;
     case FDW_F16:
       closure_apply_kernel<__half><<<grid_for(vol), 256, 0, st>>>(c->ia2, c->pb + kOffW3, c->pf + kOffB3, c->base, c->s_dev,
-                                                                  (__half *)unew, d, nb, nx, ny, nz);
+                                                                  (__half *)unew, d, nb, nx, ny, nz, factor);
       break;
     default: return cudaErrorInvalidValue;
   }

@@ -1115,9 +1115,14 @@ extern "C" int fdw_get_adjoint_wavefield(const fdw_solver *cs, int level, float 
 }
 
 extern "C" int fdw_step_closure(fdw_solver *s, fdw_closure *c, int nsteps) {
+  return fdw_step_closure_every(s, c, nsteps, 1);
+}
+
+extern "C" int fdw_step_closure_every(fdw_solver *s, fdw_closure *c, int nsteps, int every) {
   if (!s || !c) return fail(FDW_ERR_INVALID_ARG, "NULL solver or closure");
   if (s->eq != FDW_ACOUSTIC) return fail(FDW_ERR_INVALID_ARG, "the closure corrects the acoustic step");
   if (nsteps < 0) return fail(FDW_ERR_INVALID_ARG, "nsteps < 0");
+  if (every < 1) return fail(FDW_ERR_INVALID_ARG, "every must be >= 1");
   if (!s->dt_set) return fail(FDW_ERR_STATE, "fdw_set_dt must come before fdw_step_closure");
   DeviceGuard g(s->device);
   int rc = build_maps(s);
@@ -1129,11 +1134,15 @@ extern "C" int fdw_step_closure(fdw_solver *s, fdw_closure *c, int nsteps) {
   const size_t fb = s->d.vol() * s->el;
   for (int n = 0; n < nsteps; ++n) {
     const int cur = s->cur, nxt = 1 - cur;
-    CK(closure_infer_pre(c, s->storage, s->f[0][cur], s->f[0][nxt], s->vp, s->nx, s->ny, s->nz, s->nb,
-                         s->d, s->stream));
+    const bool corr = (n % every) == 0;
+    if (corr)
+      CK(closure_infer_pre(c, s->storage, s->f[0][cur], s->f[0][nxt], s->vp, s->nx, s->ny, s->nz, s->nb,
+                           s->d, s->stream));
     rc = enqueue_stencil(s, cur, s->stream);
     if (rc) return rc;
-    CK(closure_infer_apply(c, s->storage, s->f[0][nxt], s->d, s->nx, s->ny, s->nz, s->nb, s->stream));
+    if (corr)
+      CK(closure_infer_apply(c, s->storage, s->f[0][nxt], s->d, s->nx, s->ny, s->nz, s->nb, (float)every,
+                             s->stream));
     rc = enqueue_sparse(s, cur, s->stream);
     if (rc) return rc;
     s->cur = nxt;

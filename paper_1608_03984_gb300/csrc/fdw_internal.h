@@ -210,10 +210,10 @@ cudaError_t closure_infer_base(ClosureNet *c, const float *vp, int nx, int ny, i
 cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const void *um,
                               const float *vp, int nx, int ny, int nz, int nb, Dims d,
                               cudaStream_t st);
-// After the stencil: u_{n+1} += s * (last layer - base) on the physical
-// points (sponge width nb, physical extents nx, ny, nz).
+// After the stencil: u_{n+1} += factor * s * (last layer - base) on the
+// physical points (sponge width nb, physical extents nx, ny, nz).
 cudaError_t closure_infer_apply(ClosureNet *c, int storage, void *unew, Dims d, int nx, int ny, int nz, int nb,
-                                cudaStream_t st);
+                                float factor, cudaStream_t st);
 int closure_reserve_infer(ClosureNet *c, Dims d);
 // tensor-core path (closure_tc.cu)
 int closure_tc_reserve(ClosureNet *c, Dims d);

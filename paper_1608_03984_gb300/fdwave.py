@@ -77,6 +77,7 @@ _SIGS = {
     "fdw_closure_loss_grad": ([_P, _P, _P, _I, _I, _P, _P], _I),
     "fdw_closure_adam_step": ([_P, _P, _P, _I, _I, ctypes.c_float, _P], _I),
     "fdw_step_closure": ([_P, _P, _I], _I),
+    "fdw_step_closure_every": ([_P, _P, _I, _I], _I),
     "fdw_profile_begin": ([_P, _I], _I),
     "fdw_profile_end": ([_P, ctypes.POINTER(_D), ctypes.POINTER(_I)], _I),
 }
@@ -372,9 +373,14 @@ class Solver:
         _chk(lib().fdw_step(self._h, int(n)))
         return self
 
-    def step_closure(self, closure, n=1):
-        """n steps with the learned closure applied after every update."""
-        _chk(lib().fdw_step_closure(self._h, closure._h, int(n)))
+    def step_closure(self, closure, n=1, every=1):
+        """n steps with the learned closure applied after every update, or
+        (every > 1) on every `every`-th step with the correction times
+        `every` (the others are plain steps)."""
+        if int(every) == 1:
+            _chk(lib().fdw_step_closure(self._h, closure._h, int(n)))
+        else:
+            _chk(lib().fdw_step_closure_every(self._h, closure._h, int(n), int(every)))
         return self
 
     def check(self, finite=True):

@@ -202,6 +202,33 @@ def test_step_closure_matches_oracle(fdw, O):
     solver.close()
 
 
+def test_step_closure_every_second_step_matches_oracle(fdw, O):
+    """Closure on every second step with the correction doubled
+    (fdw_step_closure_every) against the oracle's sequence closure step with
+    the last layer times 2 (exact in BF16), plain step, closure step, plain
+    step; FP32 inference kernels."""
+    from paper_1608_03984_gb300 import closure
+    solver, setup, vp, src, wav, u0, um = _coarse_case(fdw, O, 33)
+    p = random_params(9, scale=0.3)
+    p2 = closure.scale_last_layer(p, 2.0).astype(np.float64)
+    net = fdw.Closure()
+    net.set_variant(1)
+    net.set_params(p)
+    solver.step_closure(net, 4, every=2)
+    ref_u, ref_um = u0.astype(np.float64), um.astype(np.float64)
+    for k in range(4):
+        if k % 2 == 0:
+            nxt = O.closure_step(setup, ref_u, ref_um, vp, p2, src, [wav[k]])
+        else:
+            nxt = O.acoustic_step(setup, ref_u, ref_um, src, [wav[k]])
+        ref_um, ref_u = ref_u, nxt
+    assert rel(solver.wavefield(0, 0), ref_u) < 4e-5
+    assert rel(solver.wavefield(0, 1), ref_um) < 4e-5
+    assert solver.current_step == 4
+    net.close()
+    solver.close()
+
+
 def test_step_closure_zero_network_equals_plain_step(fdw, O):
     """All-zero parameters: fdw_step_closure gives fdw_step's levels."""
     a, *_ = _coarse_case(fdw, O, 41)
