@@ -84,13 +84,13 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_sha():
+def kernel_source_sha(root=ROOT):
     """Hash of the acoustic stencil kernel's source (template + dispatch + PTX
     helpers), comments and white space removed: any change of the code
     changes it, an edit of a comment does not."""
     h = hashlib.sha256()
     for f in ("acoustic.cu", "acoustic_kernel.cuh", "ptx.cuh"):
-        with open(os.path.join(ROOT, "paper_1608_03984_gb300", "csrc", f)) as fh:
+        with open(os.path.join(root, "paper_1608_03984_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
@@ -98,15 +98,15 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_point():
+def ncu_traffic_per_point(root=ROOT):
     """{order: DRAM bytes per point} of the stencil kernel at 592^3 from the
     committed ncu summary, if its kernel-source hash matches the source."""
-    path = os.path.join(ROOT, "profiles", "acoustic_step_592_dram.md")
+    path = os.path.join(root, "profiles", "acoustic_step_592_dram.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"source_sha=([0-9a-f]+)", text)
-    if not m or m.group(1) != kernel_source_sha():
+    if not m or m.group(1) != kernel_source_sha(root):
         return None
     out = {}
     for o, v in re.findall(r"TRAFFIC_BYTES_PER_POINT order=(\d+) ([0-9.]+)", text):
