@@ -40,3 +40,16 @@ def test_traffic_summary_is_used_only_for_the_matching_source(tmp_path):
     assert bench.ncu_traffic_per_point(str(tmp_path)) is None
     summary.unlink()
     assert bench.ncu_traffic_per_point(str(tmp_path)) is None
+
+
+def test_closure_operating_point():
+    """The largest k whose field error stays within 5% of the every-step
+    closure's; k = 1 when no sub-cycled run qualifies."""
+    ms = {"fine": 1000.0, "closure": 1000.0}
+    sub = {"2": {"error_vs_fine": {"field": 0.0101}, "speedup_vs_fine": 1.9},
+           "4": {"error_vs_fine": {"field": 0.0104}, "speedup_vs_fine": 3.4},
+           "8": {"error_vs_fine": {"field": 0.0300}, "speedup_vs_fine": 5.6}}
+    op = bench.operating_point(0.0100, ms, sub)
+    assert op == {"every": 4, "field_error": 0.0104, "speedup_vs_fine": 3.4}
+    bad = {k: {"error_vs_fine": {"field": 0.05}, "speedup_vs_fine": 9.0} for k in ("2", "4")}
+    assert bench.operating_point(0.0100, ms, bad)["every"] == 1
