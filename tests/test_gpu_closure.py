@@ -352,7 +352,8 @@ def test_training_reduces_error_on_held_out_models(fdw):
     then on four held-out models the coarse run with the closure is closer
     to the restricted fine run than the coarse run alone: in the final
     wavefield and in the receiver traces, for every model, and by at least
-    15% on average."""
+    15% on average; the same holds with the correction applied on every
+    4th step only (times 4), at a quarter of the network's cost."""
     from paper_1608_03984_gb300 import closure as C
     pr = C.Pairing(n_c=96, nb_c=8, src_sigma=1.5)
     nt = pr.steps_to_cross(0.45)
@@ -363,14 +364,14 @@ def test_training_reduces_error_on_held_out_models(fdw):
     net = fdw.Closure()
     losses = C.train(net, samplers, iters=8000, batch=32, lr=3e-3)
     assert losses[-1] < 0.5 * losses[0]
-    ratios = {"field": [], "traces": []}
+    ratios = {(run, key): [] for run in ("closure", "closure_every4") for key in ("field", "traces")}
     for seed in (900, 901, 902, 903):
-        r = C.evaluate(pr, net, seed, nt)
-        for key in ratios:
-            assert r["closure"][key] < r["coarse"][key], (seed, r)
-            ratios[key].append(r["closure"][key] / r["coarse"][key])
-    for key, v in ratios.items():
-        assert np.mean(v) < 0.85, (key, v)
+        r = C.evaluate(pr, net, seed, nt, everies=(1, 4))
+        for run, key in ratios:
+            assert r[run][key] < r["coarse"][key], (seed, run, r)
+            ratios[(run, key)].append(r[run][key] / r["coarse"][key])
+    for k, v in ratios.items():
+        assert np.mean(v) < 0.85, (k, v)
     net.close()
 
 
