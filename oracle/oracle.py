@@ -13,6 +13,8 @@ the sponge constants of ``sponge_gamma_max`` / ``sponge_profile`` (reflection
 coefficient R = 1e-3, linear ramp; the tests only pin that the sponge
 absorbs), the medium extension into the sponge of ``extend`` (edge values),
 and the receiver sampling of the forward runs (nt + 1 samples, d[0] = 0).
+``extend_adjoint`` is pinned as the transpose of ``extend`` (dot test and
+the brute-force transposed matrix in the adjoint tests).
 
 Array convention: numpy arrays of shape (nz, ny, nx), C order, x fastest.
 Positions are (x, y, z) metres of the physical grid, whose first point is at

@@ -99,3 +99,41 @@ def test_gradient_in_sponge(O):
     # dJ/dc = dJ/dm * dm/dc with m = dt^2 / c: dm/dc = -dt^2 / c^2
     dJdc = g[k, j, i] * (-dt * dt / base[k, j, i] ** 2)
     assert dJdc == pytest.approx(fd, rel=1e-5), (dJdc, fd)
+
+
+@pytest.mark.parametrize("nb", [1, 3])
+def test_extend_adjoint_dot_product(O, nb):
+    """extend_adjoint is the transpose of extend (the medium's continuation
+    into the sponge, through which the FWI gradient on the computational
+    grid is folded back onto the physical grid): <E a, b> = <a, E^T b> for
+    random a, b on a non-cubic grid."""
+    rng = np.random.default_rng(7 + nb)
+    a = rng.standard_normal((5, 7, 6))
+    b = rng.standard_normal((5 + 2 * nb, 7 + 2 * nb, 6 + 2 * nb))
+    lhs = np.sum(O.extend(a, nb) * b)
+    rhs = np.sum(a * O.extend_adjoint(b, nb))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs)), (lhs, rhs)
+
+
+@pytest.mark.parametrize("nb", [0, 1, 2])
+def test_extend_adjoint_equals_transposed_matrix(O, nb):
+    """Brute force on a 4 x 5 x 6 grid: build the matrix of the extension
+    column by column (extension of each unit vector), transpose it, apply it
+    to a random computational field; extend_adjoint gives the same vector.
+    A corner sponge point counts once per physical point it copies, so a
+    missed edge or corner contribution fails here."""
+    shp = (4, 5, 6)
+    ncomp = tuple(k + 2 * nb for k in shp)
+    cols = []
+    for i in range(int(np.prod(shp))):
+        e = np.zeros(int(np.prod(shp)))
+        e[i] = 1.0
+        cols.append(O.extend(e.reshape(shp), nb).ravel())
+    M = np.stack(cols, axis=1)  # computational x physical
+    # every computational point copies exactly one physical point
+    assert M.shape == (int(np.prod(ncomp)), int(np.prod(shp)))
+    assert np.all(M.sum(axis=1) == 1.0)
+    g = np.random.default_rng(3).standard_normal(ncomp)
+    want = (M.T @ g.ravel()).reshape(shp)
+    got = O.extend_adjoint(g, nb)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13)
