@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--closure-patches", type=int, default=2000, help="patches kept per training model")
     p.add_argument("--closure-iters", type=int, default=8000)
     p.add_argument("--closure-eval", type=int, default=16, help="held-out models at full size")
+    p.add_argument("--no-config1", action="store_true")
+    p.add_argument("--details", default="bench_details.json",
+                   help="file that receives every section of the run (the printed line is the summary)")
     p.add_argument("--profile-closure-step", type=int, default=0, metavar="N",
                    help="only run 40 plain and 2 closure steps on an N^3 coarse grid (+20 sponge), "
                         "random network: the case the closure kernel is profiled on")
@@ -98,10 +101,15 @@ def kernel_source_sha(root=ROOT):
     return h.hexdigest()[:16]
 
 
+TRAFFIC_SUMMARY = "acoustic_tma_dram_336.md"
+
+
 def ncu_traffic_per_point(root=ROOT):
-    """{order: DRAM bytes per point} of the stencil kernel at 592^3 from the
-    committed ncu summary, if its kernel-source hash matches the source."""
-    path = os.path.join(root, "profiles", "acoustic_step_592_dram.md")
+    """{order: DRAM bytes per point} of the stencil kernel from the committed
+    ncu summary of the small case (336^3, one solver, one order per
+    capture), if its kernel-source hash matches the source. The bench
+    scales it to a full launch by the points of the workload."""
+    path = os.path.join(root, "profiles", TRAFFIC_SUMMARY)
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -358,7 +366,8 @@ def run_fdwave(args, orders):
     tpp = ncu_traffic_per_point()
     traffic = None
     if tpp is not None and all(o in tpp for o in orders):
-        # mean DRAM bytes per launch over the orders of the sweep (ncu, 592^3)
+        # mean DRAM bytes per launch over the orders of the sweep: bytes per
+        # point measured on the 336^3 case, times the points of one launch
         traffic = sum(tpp[o] for o in orders) / len(orders) * points
         for o in orders:
             per_order[str(o)]["ncu_dram_bytes_per_point"] = tpp[o]
@@ -388,6 +397,10 @@ def run_fdwave(args, orders):
     if not args.no_closure and world == 1:
         closure_res = run_closure(args)
 
+    cfg1 = None
+    if not args.no_config1:
+        cfg1 = run_config1(stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         samples = [oracle_sample(base.vp, base.h, base.nb, o, base.dt) for o in orders]
@@ -407,15 +420,22 @@ def run_fdwave(args, orders):
             v["measured_runtime_s"] = v["N"] * v["nt"] / (per_order[o]["kernel_gpts"] * 1e9)
 
     if rank == 0:
-        line = {
+        full = {
             "metric": "Gpts/s per timestep", "value": value, "unit": "Gpts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config_dict(args, orders, base),
             "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu, "tti": tti,
-            "fwi": fwi_res, "storage": storage, "closure": closure_res, "paper_model_gb300": paper,
-            "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
+            "fwi": fwi_res, "storage": storage, "closure": closure_res, "config1": cfg1,
+            "paper_model_gb300": paper, "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
         }
+        line = headline(full, args.details)
+        try:
+            with open(args.details, "w") as f:
+                json.dump(full, f, indent=1)
+        except OSError as e:
+            line["details"] = "not written: %s" % e
+        # the summary line is the last line of the run
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -554,7 +574,7 @@ def run_fwi(args):
     return {"workload": "fwi %d^3 + %d-point sponge (%d^3), h=15 m, order 8, %d steps, %d shots, "
                         "%d receivers, %d checkpoints/shot" % (w.n[0], w.nb, nz, w.nt, nshot,
                                                                 w.rec_xyz.shape[0], w.checkpoints),
-            "gradient_s": sec, "per_shot_s": sec / nshot, "misfit": float(J),
+            "gradient_s": sec, "per_shot_s": sec / nshot, "shots": nshot, "misfit": float(J),
             "stencil_steps": 3 * w.nt * nshot,
             "gpts_equiv": 3 * w.nt * nshot * pts / sec / 1e9,
             "gradient_finite": bool(torch.isfinite(g).all())}
@@ -659,6 +679,88 @@ def run_closure(args):
             # every-step closure's: the speed-up at (the same) stated error
             "operating_point": operating_point(err["closure"]["field"], ms, sub),
             "per_model": [{k: v for k, v in r.items() if k != "ms"} for r in evals]}
+
+
+HEADLINE_MAX_BYTES = 4096  # the summary line stays short enough to be read whole
+
+
+def _r(x, nd=4):
+    """Round to nd significant digits (None stays None)."""
+    if x is None:
+        return None
+    return float("%.*g" % (nd, x))
+
+
+def headline(full, details_path):
+    """The printed JSON line: the headline metric with its roofline, e2e,
+    CPU baseline and clocks, plus one short summary per further section; the
+    sections themselves go to the details file."""
+    keep = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+            "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "cpu_baseline",
+            "clocks", "gpu_launches")
+    line = {k: full.get(k) for k in keep}
+    if line["e2e"]:
+        line["e2e"] = {k: v for k, v in line["e2e"].items() if k != "note"}
+    line["per_order"] = {o: {"kernel_ms": _r(v["kernel_ms"]), "gpts": _r(v["kernel_gpts"]),
+                             "frac_of_measured_hbm": _r(v["frac_of_measured_hbm"])}
+                         for o, v in (full.get("per_order") or {}).items()}
+    summ = {}
+    tti = full.get("tti")
+    if tti:
+        summ["tti"] = {o: {st: {"gpts": _r(v["gpts"]), "frac": _r(v["frac_of_measured_hbm"])}
+                           for st, v in tti[o].items()} for o in tti if o.isdigit()}
+    st = full.get("storage")
+    if st:
+        summ["storage_speedup_vs_f32"] = {o: {k: _r(v["speedup_vs_f32"]) for k, v in st[o].items()}
+                                          for o in st if o.isdigit()}
+    fw = full.get("fwi")
+    if fw:
+        summ["fwi"] = {"gradient_s": _r(fw["gradient_s"]), "per_shot_s": _r(fw["per_shot_s"]),
+                       "shots": fw["shots"]}
+    cl = full.get("closure")
+    if cl:
+        summ["closure"] = {
+            "field_error_vs_fine": {m: _r(v["field"]) for m, v in cl["error_vs_fine"].items()},
+            "speedup_vs_fine_every_step": _r(cl["speedup_vs_fine"]["closure"]),
+            "operating_point": {k: _r(v) for k, v in cl["operating_point"].items()}}
+    c1 = full.get("config1")
+    if c1:
+        summ["config1"] = {"gpts": _r(c1["gpts"]), "ms_per_run": _r(c1["ms_per_run"])}
+    line["sections"] = summ
+    line["details"] = os.path.basename(details_path)
+    return line
+
+
+def run_config1(stream, reps=5):
+    """The two-layer 64^3 workload (+ 10-point sponge = 84^3, order 4, 200
+    steps, 32 receivers) through the CUDA-graph time loop: launch-bound, so
+    this is the per-step overhead figure. Gpts/s over the 200-step run
+    (CUDA events, mean of `reps` runs after one warm-up run)."""
+    import torch
+    from paper_1608_03984_gb300 import fdwave, synth
+    w = synth.two_layer()
+    s = fdwave.Solver(w.n, w.h, w.nb, w.order, stream=stream)
+    s.set_model(w.vp).set_dt(w.dt).set_sources(w.src_xyz, w.wavelet).set_receivers(w.rec_xyz, w.nt)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    times = []
+    for rep in range(reps + 1):
+        s.reset()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(w.nt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep:
+            times.append(e0.elapsed_time(e1))
+    s.check()
+    s.close()
+    ms = sum(times) / len(times)
+    nz, ny, nx = (k + 2 * w.nb for k in w.n)
+    return {"workload": "two_layer %d^3 + %d-point sponge (%d^3), order %d, %d steps, %d receivers"
+                        % (w.n[0], w.nb, nz, w.order, w.nt, w.rec_xyz.shape[0]),
+            "ms_per_run": ms, "us_per_step": 1e3 * ms / w.nt,
+            "gpts": nz * ny * nx * w.nt / (ms / 1e3) / 1e9}
 
 
 def run_e2e(args, orders, base, stream):

@@ -310,7 +310,10 @@ int fdw_misfit(const double *d, const double *d_obs, long long n, double *residu
  * the one scratch array of the device: calls that overlap on the GPU race
  * and must be serialised by the caller (e.g. issue them on one stream).
  * Nothing in the scratch needs clearing between calls (every chunk sum a
- * call reads, that call writes first).
+ * call reads, that call writes first). The looked-up address is kept for
+ * the life of the process: do not use this entry point on a device after
+ * cudaDeviceReset of that device (the module may be loaded again at
+ * another address).
  * Errors: INVALID_ARG (NULL pointers, n < 0, n above the limit), CUDA.
  */
 int fdw_misfit_noalloc(const double *d, const double *d_obs, long long n, double *residual,
@@ -394,10 +397,13 @@ int fdw_step_closure(fdw_solver *s, fdw_closure *c, int nsteps);
 
 /*
  * fdw_step_closure with the correction applied only on every `every`-th
- * step of the call (steps 0, every, 2 every, ...; the others are plain
- * steps) and multiplied by `every` there, so that the correction per unit
- * of time stays the same at 1/every of the network's cost. every = 1 is
- * fdw_step_closure. Errors: as fdw_step_closure; INVALID_ARG for every < 1.
+ * step (the steps whose solver step count n, fdw_current_step before the
+ * step, is a multiple of `every`; the others are plain steps) and
+ * multiplied by `every` there, so that the correction per unit of time
+ * stays the same at 1/every of the network's cost. The phase follows the
+ * solver's step count, not the call: two calls of m steps correct the same
+ * steps as one call of 2m. every = 1 is fdw_step_closure. Errors: as
+ * fdw_step_closure; INVALID_ARG for every < 1.
  */
 int fdw_step_closure_every(fdw_solver *s, fdw_closure *c, int nsteps, int every);
 

@@ -1134,7 +1134,9 @@ extern "C" int fdw_step_closure_every(fdw_solver *s, fdw_closure *c, int nsteps,
   const size_t fb = s->d.vol() * s->el;
   for (int n = 0; n < nsteps; ++n) {
     const int cur = s->cur, nxt = 1 - cur;
-    const bool corr = (n % every) == 0;
+    // the phase follows the solver's step count, so chunked calls correct
+    // the same steps as one call over the same interval
+    const bool corr = ((s->it + n) % every) == 0;
     if (corr)
       CK(closure_infer_pre(c, s->storage, s->f[0][cur], s->f[0][nxt], s->vp, s->nx, s->ny, s->nz, s->nb,
                            s->d, s->stream));

@@ -229,6 +229,33 @@ def test_step_closure_every_second_step_matches_oracle(fdw, O):
     solver.close()
 
 
+def test_step_closure_every_phase_follows_the_step_count(fdw, O):
+    """The every-k closure corrects the steps whose solver step count is a
+    multiple of k: two calls of 2 steps with every = 4 give the levels of
+    one call of 4 steps (one correction, at step 0), and a call that starts
+    at step 2 corrects nothing until step 4."""
+    a, *_ = _coarse_case(fdw, O, 45)
+    b, *_ = _coarse_case(fdw, O, 45)
+    c, *_ = _coarse_case(fdw, O, 45)
+    net = fdw.Closure()
+    net.set_variant(1)
+    net.set_params(random_params(10, scale=0.3))
+    a.step_closure(net, 4, every=4)
+    b.step_closure(net, 2, every=4)
+    b.step_closure(net, 2, every=4)
+    np.testing.assert_array_equal(a.wavefield(0, 0), b.wavefield(0, 0))
+    np.testing.assert_array_equal(a.wavefield(0, 1), b.wavefield(0, 1))
+    # steps 0, 1 plain, then steps 2, 3 through the closure call: no correction
+    d, *_ = _coarse_case(fdw, O, 45)
+    c.step(4)
+    d.step(2)
+    d.step_closure(net, 2, every=4)
+    np.testing.assert_array_equal(c.wavefield(0, 0), d.wavefield(0, 0))
+    net.close()
+    for s in (a, b, c, d):
+        s.close()
+
+
 def test_step_closure_zero_network_equals_plain_step(fdw, O):
     """All-zero parameters: fdw_step_closure gives fdw_step's levels."""
     a, *_ = _coarse_case(fdw, O, 41)
