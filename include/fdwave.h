@@ -208,10 +208,10 @@ int fdw_set_zchunks(fdw_solver *s, int zchunks);
 
 /*
  * Tile configuration of the 2.5D kernel: acoustic (points per thread in x/y,
- * warps per CTA, z unrolling; acoustic_kernel.cuh) or TTI (warps per CTA, z
- * unrolling; tti_kernel.cuh): acoustic 0..5, TTI 0..8, or -1 for the
- * default of the solver's equation, order and storage. Resets zchunks to
- * its default.
+ * warps per CTA, z unrolling, planes per CTA barrier; acoustic_kernel.cuh)
+ * or TTI (warps per CTA, z unrolling; tti_kernel.cuh): acoustic 0..11, TTI
+ * 0..8, or -1 for the default of the solver's equation, order and storage.
+ * Resets zchunks to its default.
  * fdw_get_tile_config returns the configuration in use (-1 for NULL).
  * Errors: INVALID_ARG.
  */
@@ -272,6 +272,16 @@ int fdw_adjoint_current_step(const fdw_solver *s);
  * Errors: STATE (no gradient accumulated).
  */
 int fdw_get_gradient(fdw_solver *s, double *grad_m, int ptr_is_device);
+
+/*
+ * Velocity gradient from the slowness-squared gradient (m = 1/v^2, so
+ * dJ/dv = -2 v^-3 dJ/dm), elementwise over n points: vp FP32 m/s, grad_m
+ * and grad_v FP64, all in device memory (grad_v may alias grad_m);
+ * asynchronous on `stream`. Used by the FWI gradient after the per-shot
+ * dJ/dm of fdw_get_gradient have been summed.
+ * Errors: INVALID_ARG (NULL pointers with n > 0, n < 0), CUDA.
+ */
+int fdw_velocity_gradient(const float *vp, const double *grad_m, long long n, double *grad_v, void *stream);
 
 /* dJ/d wavelet [nt][nsrc] FP64 of the adjoint run so far (host or device). */
 int fdw_get_source_adjoint(fdw_solver *s, double *out, int ptr_is_device);

@@ -114,11 +114,12 @@ int acoustic_geom(int storage, int r, int tile, TileGeom *g) {
 }
 
 // Default configuration per (storage, radius): the fastest on the 592^3
-// workload in sweeps of every configuration and z chunking at orders 2, 4,
-// 8, 12 and 16 (radii 3, 5 and 7 take a neighbour's choice).
+// workload in sweeps of the configurations (default z chunking) at every
+// even order 2-16 for FP32 and at orders 2, 4, 8, 12, 16 for 16-bit
+// storage (radii 3, 5 and 7 take a neighbour's choice there).
 int acoustic_default_tile(int storage, int r) {
-  static const int best32[kMaxR + 1] = {1, 1, 3, 1, 1, 3, 3, 3, 1};
-  static const int best16[kMaxR + 1] = {1, 1, 1, 1, 1, 5, 5, 1, 1};
+  static const int best32[kMaxR + 1] = {1, 1, 3, 3, 10, 10, 10, 10, 6};
+  static const int best16[kMaxR + 1] = {1, 1, 1, 1, 1, 5, 5, 5, 5};
   if (r < 1 || r > kMaxR) return 1;
   return storage == FDW_F32 ? best32[r] : best16[r];
 }

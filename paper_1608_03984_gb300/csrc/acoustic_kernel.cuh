@@ -52,6 +52,7 @@ template <> struct Pk<1> {
   static __device__ __forceinline__ E splat(float a) { return a; }
   static __device__ __forceinline__ E make(float a, float) { return a; }
   static __device__ __forceinline__ float &at(E &e, int) { return e; }
+  static __device__ __forceinline__ float get(const E &e, int) { return e; }
   static __device__ __forceinline__ E wt(const Weights &w, int m) { return w.w2[m]; }
 };
 template <> struct Pk<2> {
@@ -62,10 +63,11 @@ template <> struct Pk<2> {
   static __device__ __forceinline__ E splat(float a) { return make_float2(a, a); }
   static __device__ __forceinline__ E make(float a, float b) { return make_float2(a, b); }
   static __device__ __forceinline__ float &at(E &e, int i) { return i ? e.y : e.x; }
+  static __device__ __forceinline__ float get(const E &e, int i) { return i ? e.y : e.x; }
   static __device__ __forceinline__ E wt(const Weights &w, int m) { return w.w2p[m]; }
 };
 
-template <typename T, int R, int RX, int RY, int BY, int NS, int U>
+template <typename T, int R, int RX, int RY, int BY, int NS, int U, int BP = 1>
 struct AcTile {
   static constexpr int TX = 32 * RX;
   static constexpr int TY = BY * RY;
@@ -84,6 +86,7 @@ struct AcTile {
   static constexpr int THREADS = 32 * BY;
   static constexpr int QL = 2 * R + U;
   static_assert(NS >= 2, "ring needs two stages");
+  static_assert(BP >= 1 && U % BP == 0 && NS > BP, "barrier period divides the unroll, ring deeper than it");
   static_assert(BXH <= 256 && BYH <= 256 && TX <= 256 && TY <= 256, "TMA box dimension limit");
   static_assert((BXH * EL) % 16 == 0 && (TX * EL) % 16 == 0, "TMA inner box bytes");
   static_assert((HX * EL) % 16 == 0, "TMA x coordinate alignment");
@@ -91,14 +94,14 @@ struct AcTile {
   static_assert(SMEM_B <= 227 * 1024, "shared memory per CTA");
 };
 
-template <typename T, int R, int RX, int RY, int BY, int NS, int U>
+template <typename T, int R, int RX, int RY, int BY, int NS, int U, int BP>
 __global__ void __launch_bounds__(32 * BY)
     acoustic_tma_kernel(const __grid_constant__ CUtensorMap m_halo,
                         const __grid_constant__ CUtensorMap m_head,
                         const __grid_constant__ CUtensorMap m_prev,
                         const __grid_constant__ CUtensorMap m_c, T *__restrict__ out, Dims d,
                         Weights w, Sponge sp, int zc, int *err) {
-  using C = AcTile<T, R, RX, RY, BY, NS, U>;
+  using C = AcTile<T, R, RX, RY, BY, NS, U, BP>;
   using V = Vec<T, RX>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -177,6 +180,9 @@ __global__ void __launch_bounds__(32 * BY)
 
   const E wc = P::splat(3.f * w.w2[0]);
   const size_t plane = d.plane();
+  // a bounded wait that gave up between barriers (BP > 1)
+  bool bad = false;
+  int bad_at = 0;
 
 #pragma unroll 1
   for (int j0 = 0; j0 < nit; j0 += U) {
@@ -186,16 +192,29 @@ __global__ void __launch_bounds__(32 * BY)
       if (j >= nit) break;  // uniform
       const int s = j % NS;
       const bool ok = mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((j / NS) & 1));
-      // Also the point where every thread has finished iteration j-1.
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) {
-          atomicOr(err, kErrWaitTimeout);
-          for (int jj = j; jj <= issued_hi; ++jj)
-            (void)mbar_wait_bounded(smem_u32(&bars[jj % NS]), (uint32_t)((jj / NS) & 1));
+      if (u % BP == 0) {
+        // The CTA barrier, every BP planes: every thread has finished the
+        // iterations before j, so their BP stages can be refilled.
+        if (__syncthreads_or(bad || !ok)) {
+          if (tid == 0) {
+            atomicOr(err, kErrWaitTimeout);
+            for (int jj = bad_at; jj <= issued_hi; ++jj)
+              (void)mbar_wait_bounded(smem_u32(&bars[jj % NS]), (uint32_t)((jj / NS) & 1));
+          }
+          return;
         }
-        return;
+        if (tid == 0) {
+#pragma unroll
+          for (int k = BP; k >= 1; --k)
+            if (j - k >= 0 && j - k + NS < nit) issue(j - k + NS);
+        }
+      } else if (!ok && !bad) {
+        // the CTA leaves at the next barrier; until then this thread's
+        // results are not valid (the error flag says so) but every access
+        // stays inside the tile and the output field
+        bad = true;
+        bad_at = j;
       }
-      if (tid == 0 && j >= 1 && j - 1 + NS < nit) issue(j - 1 + NS);
 
       const unsigned char *st = smem + s * C::STAGE_B;
       const int zh = z0 - R + j;
@@ -281,23 +300,29 @@ __global__ void __launch_bounds__(32 * BY)
           }
         }
       }
-      // update and store; 1/P by the fast reciprocal (<= 2 ulp; exactly 1
-      // outside the sponge)
+      // update and store: u+ = (2u - (1 - g) u- + c lap u) / (1 + g) with
+      // g = gamma dt / 2; 1/(1 + g) by the fast reciprocal (<= 2 ulp;
+      // exactly 1 outside the sponge). Pairs of points on f32x2.
       const float ghz = gzs[zo - z0];
 #pragma unroll
       for (int ry = 0; ry < RY; ++ry) {
         const int yl = ty * RY + ry;
         const V vm = *(const V *)(PV + yl * C::TX + xl);
         const V vc = *(const V *)(CC + yl * C::TX + xl);
+        const float gyz = gyr[ry] + ghz;
         V res;
 #pragma unroll
-        for (int rx = 0; rx < RX; ++rx) {
-          const float gh = gxr[rx] + gyr[ry] + ghz;
-          const float uc = P::at(q[ry][rx / W][u + R], rx % W);
-          const float up = (2.f * uc - (1.f - gh) * St<T>::ld(vm.v[rx]) +
-                            St<T>::ld(vc.v[rx]) * P::at(acc[ry][rx / W], rx % W)) *
-                           __fdividef(1.f, 1.f + gh);
-          res.v[rx] = St<T>::st(up);
+        for (int k = 0; k < NK; ++k) {
+          const E gh = P::add(P::make(gxr[W * k], gxr[W * k + W - 1]), P::splat(gyz));
+          const E uc = q[ry][k][u + R];
+          E t = P::fma(P::make(St<T>::ld(vc.v[W * k]), St<T>::ld(vc.v[W * k + W - 1])), acc[ry][k],
+                       P::add(uc, uc));
+          t = P::fma(P::add(gh, P::splat(-1.f)), P::make(St<T>::ld(vm.v[W * k]), St<T>::ld(vm.v[W * k + W - 1])),
+                     t);
+          const E up = P::mul(t, P::make(__fdividef(1.f, 1.f + P::get(gh, 0)),
+                                         __fdividef(1.f, 1.f + P::get(gh, W - 1))));
+#pragma unroll
+          for (int i = 0; i < W; ++i) res.v[W * k + i] = St<T>::st(P::get(up, i));
         }
         const int x = x0 + xl, y = y0 + yl;
         if (y < d.NY) {
@@ -320,13 +345,19 @@ __global__ void __launch_bounds__(32 * BY)
 #pragma unroll
         for (int i = 0; i < 2 * R; ++i) q[ry][k][i] = q[ry][k][i + U];
   }
+  if (bad) {  // gave up after the last barrier
+    atomicOr(err, kErrWaitTimeout);
+    if (tid == 0)
+      for (int jj = bad_at; jj <= issued_hi; ++jj)
+        (void)mbar_wait_bounded(smem_u32(&bars[jj % NS]), (uint32_t)((jj / NS) & 1));
+  }
 }
 
 // Host-side launch of one configuration.
-template <typename T, int R, int RX, int RY, int BY, int NS, int U>
+template <typename T, int R, int RX, int RY, int BY, int NS, int U, int BP>
 cudaError_t launch_acoustic_cfg(const AcousticLaunch &L, cudaStream_t st) {
-  using C = AcTile<T, R, RX, RY, BY, NS, U>;
-  auto kern = acoustic_tma_kernel<T, R, RX, RY, BY, NS, U>;
+  using C = AcTile<T, R, RX, RY, BY, NS, U, BP>;
+  auto kern = acoustic_tma_kernel<T, R, RX, RY, BY, NS, U, BP>;
   if (L.prepare_only) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_B);
     if (e == cudaSuccess && L.occupancy_out)
@@ -343,9 +374,9 @@ cudaError_t launch_acoustic_cfg(const AcousticLaunch &L, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int R, int RX, int RY, int BY, int NS, int U>
+template <typename T, int R, int RX, int RY, int BY, int NS, int U, int BP>
 void tile_cfg(TileGeom *g) {
-  using C = AcTile<T, R, RX, RY, BY, NS, U>;
+  using C = AcTile<T, R, RX, RY, BY, NS, U, BP>;
   g->box_halo_x = C::BXH;
   g->box_halo_y = C::BYH;
   g->box_int_x = C::TX;
@@ -353,15 +384,22 @@ void tile_cfg(TileGeom *g) {
   g->smem = C::SMEM_B;
 }
 
-// Candidate configurations (RX, RY, BY, U), selected at run time by index.
-#define FDW_AC_CFGS(X) \
-  X(0, 1, 4, 4, 1)     \
-  X(1, 4, 2, 4, 4)     \
-  X(2, 4, 1, 8, 4)     \
-  X(3, 2, 2, 8, 4)     \
-  X(4, 4, 2, 8, 2)     \
-  X(5, 4, 2, 4, 2)
-constexpr int kAcNS = 4;
+// Candidate configurations (RX, RY, BY, U, BP, NS), selected at run time by
+// index; BP = planes per CTA barrier, NS = TMA ring stages (3 stages leave
+// room for a third CTA per SM where the registers allow it).
+#define FDW_AC_CFGS(X)    \
+  X(0, 1, 4, 4, 1, 1, 4)  \
+  X(1, 4, 2, 4, 4, 1, 4)  \
+  X(2, 4, 1, 8, 4, 1, 4)  \
+  X(3, 2, 2, 8, 4, 1, 4)  \
+  X(4, 4, 2, 8, 2, 1, 4)  \
+  X(5, 4, 2, 4, 2, 1, 4)  \
+  X(6, 4, 2, 4, 4, 2, 4)  \
+  X(7, 2, 2, 8, 4, 2, 4)  \
+  X(8, 4, 1, 8, 4, 2, 4)  \
+  X(9, 4, 2, 4, 4, 2, 3)  \
+  X(10, 4, 2, 4, 4, 1, 3) \
+  X(11, 2, 2, 8, 4, 2, 3)
 
 // Per-storage dispatch over radius and configuration (one TU per storage).
 #define FDW_AC_DEFINE_STORAGE(SUFFIX, TYPE)                                                   \
@@ -410,7 +448,7 @@ constexpr int kAcNS = 4;
 
 // Case bodies used by FDW_AC_DEFINE_STORAGE; StorageT is defined by the
 // including translation unit.
-#define FDW_AC_CASE_LAUNCH(ID, RX, RY, BY, U) \
-  case ID: return launch_acoustic_cfg<StorageT, R, RX, RY, BY, kAcNS, U>(L, st);
-#define FDW_AC_CASE_GEOM(ID, RX, RY, BY, U) \
-  case ID: tile_cfg<StorageT, R, RX, RY, BY, kAcNS, U>(g); return 0;
+#define FDW_AC_CASE_LAUNCH(ID, RX, RY, BY, U, BP, NS) \
+  case ID: return launch_acoustic_cfg<StorageT, R, RX, RY, BY, NS, U, BP>(L, st);
+#define FDW_AC_CASE_GEOM(ID, RX, RY, BY, U, BP, NS) \
+  case ID: tile_cfg<StorageT, R, RX, RY, BY, NS, U, BP>(g); return 0;

@@ -94,7 +94,8 @@ struct fdw_solver {
   CUtensorMap map_halo[2][2], map_int[2][2], map_c;  // [field][buffer]
   CUtensorMap map_e, map_dl, map_ax, map_ay;          // TTI medium
   bool maps_ok = false;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};      // one step, per buffer parity
+  cudaGraphExec_t graph_run[2] = {nullptr, nullptr};  // kGraphSteps steps, per parity
   bool graph_ok = false;
 
   // profiling: CUDA events around each stencil launch (direct launches)
@@ -243,11 +244,16 @@ int build_maps(fdw_solver *s) {
 }
 
 void drop_graphs(fdw_solver *s) {
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b) {
     if (s->graph[b]) {
       cudaGraphExecDestroy(s->graph[b]);
       s->graph[b] = nullptr;
     }
+    if (s->graph_run[b]) {
+      cudaGraphExecDestroy(s->graph_run[b]);
+      s->graph_run[b] = nullptr;
+    }
+  }
   s->graph_ok = false;
 }
 
@@ -752,19 +758,25 @@ static int ensure_graphs(fdw_solver *s) {
   // kernel attributes (large dynamic shared memory) are set outside capture
   CK(s->eq == FDW_ACOUSTIC ? acoustic_prepare(s->storage, s->r, s->tile)
                            : tti_prepare(s->storage, s->r, s->tile));
+  // per buffer parity b: one step, and a run of kGraphSteps steps (an even
+  // number, so the run ends on parity b again); the sparse kernels read the
+  // step from the device counter, so a graph serves every step
   for (int b = 0; b < 2; ++b) {
-    cudaGraph_t gr = nullptr;
-    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_step(s, b, s->cap);
-    cudaError_t e = cudaStreamEndCapture(s->cap, &gr);
-    if (rc) {
-      if (gr) cudaGraphDestroy(gr);
-      return rc;
+    for (int run = 0; run < 2; ++run) {
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+      const int n = run ? kGraphSteps : 1;
+      for (int i = 0; i < n && !rc; ++i) rc = enqueue_step(s, (b + i) & 1, s->cap);
+      cudaError_t e = cudaStreamEndCapture(s->cap, &gr);
+      if (rc) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(run ? &s->graph_run[b] : &s->graph[b], gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     }
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&s->graph[b], gr, 0);
-    cudaGraphDestroy(gr);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   }
   s->graph_ok = true;
   return FDW_OK;
@@ -847,6 +859,12 @@ extern "C" int fdw_step(fdw_solver *s, int nsteps) {
   if (s->hist_on && !s->prof && s->eq == FDW_ACOUSTIC) return step_into_history(s, nsteps);
   const size_t fb = s->d.vol() * s->el;
   for (int n = 0; n < nsteps; ++n) {
+    if (!s->prof && !s->hist_on && nsteps - n >= kGraphSteps) {
+      // kGraphSteps steps in one launch (the parity is unchanged after it)
+      CK(cudaGraphLaunch(s->graph_run[s->cur], s->stream));
+      n += kGraphSteps - 1;
+      continue;
+    }
     if (s->prof && (size_t)(2 * s->prof_n + 1) < s->ev.size()) {
       CK(cudaEventRecord(s->ev[2 * s->prof_n], s->stream));
       rc = enqueue_stencil(s, s->cur, s->stream);

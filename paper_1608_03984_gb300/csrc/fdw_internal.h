@@ -12,7 +12,7 @@ namespace fdw {
 
 constexpr int kMaxR = 8;          // space order 16
 constexpr int kTileX = 32;        // x extent of a stencil tile (one warp)
-constexpr int kMaxZChunk = 1024;  // most z planes one CTA of a 2.5D kernel marches
+constexpr int kMaxZChunk = 256;  // most z planes one CTA of a 2.5D kernel marches
 
 // Device error flags (bit mask written with atomicOr).
 constexpr int kErrWaitTimeout = 1;  // an mbarrier wait gave up
@@ -94,7 +94,8 @@ int tti_ctas_per_sm(int storage, int r, int tile);
 struct TileGeom {
   int box_halo_x, box_halo_y, box_int_x, box_int_y, smem;
 };
-constexpr int kAcTiles = 6;  // number of configurations (see acoustic_kernel.cuh)
+constexpr int kGraphSteps = 16;  // steps per CUDA graph of a long fdw_step run (even)
+constexpr int kAcTiles = 12;  // number of configurations (see acoustic_kernel.cuh)
 // 0 on success, -1 for an unknown (storage, r, tile).
 int acoustic_geom(int storage, int r, int tile, TileGeom *g);
 // Default configuration for (storage, r).

@@ -57,6 +57,17 @@ __global__ void __launch_bounds__(kMisfitThreads)
 
 long long misfit_chunks(long long n) { return (n + kMisfitChunk - 1) / kMisfitChunk; }
 
+// dJ/dv = dJ/dm dm/dv with m = 1/v^2: -2 v^-3 dJ/dm, elementwise in FP64.
+__global__ void __launch_bounds__(256)
+    velocity_gradient_kernel(const float *__restrict__ v, const double *__restrict__ gm, long long n,
+                             double *__restrict__ gv) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double vi = (double)v[i];
+    gv[i] = -2.0 * gm[i] / (vi * vi * vi);
+  }
+}
+
 cudaError_t launch_misfit(const double *d, const double *o, long long n, double *res, double *J,
                           double *partial, cudaStream_t st) {
   const long long nc = misfit_chunks(n);
@@ -150,5 +161,18 @@ extern "C" int fdw_misfit(const double *d, const double *d_obs, long long n, dou
     return report_error(FDW_ERR_CUDA, "fdw_misfit: %s",
                         cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
+  return FDW_OK;
+}
+
+extern "C" int fdw_velocity_gradient(const float *vp, const double *grad_m, long long n, double *grad_v,
+                                     void *stream) {
+  if (n < 0 || (n > 0 && (!vp || !grad_m || !grad_v)))
+    return report_error(FDW_ERR_INVALID_ARG, "fdw_velocity_gradient: NULL pointer or n < 0");
+  if (n == 0) return FDW_OK;
+  long long blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  velocity_gradient_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(vp, grad_m, n, grad_v);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return report_error(FDW_ERR_CUDA, "fdw_velocity_gradient: %s", cudaGetErrorString(e));
   return FDW_OK;
 }

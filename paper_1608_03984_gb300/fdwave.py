@@ -67,6 +67,7 @@ _SIGS = {
     "fdw_get_adjoint_wavefield": ([_P, _I, _P, _I], _I),
     "fdw_misfit": ([_P, _P, ctypes.c_longlong, _P, _P, _P], _I),
     "fdw_misfit_noalloc": ([_P, _P, ctypes.c_longlong, _P, _P, _P], _I),
+    "fdw_velocity_gradient": ([_P, _P, ctypes.c_longlong, _P, _P], _I),
     "fdw_closure_num_params": ([], ctypes.c_longlong),
     "fdw_closure_create": ([ctypes.POINTER(_P), _P], _I),
     "fdw_closure_destroy": ([_P], _I),
@@ -182,6 +183,23 @@ def misfit(d, d_obs, residual=None, J=None, stream=None):
     _chk(lib().fdw_misfit(_cuda_f64(d, "d"), _cuda_f64(d_obs, "d_obs"), n, rp,
                           _cuda_f64(J, "J"), _stream_handle(stream)))
     return J
+
+
+def velocity_gradient(vp, grad_m, out=None, stream=None):
+    """dJ/dv = -2 v^-3 dJ/dm by fdw_velocity_gradient: vp a float32 CUDA
+    tensor, grad_m a float64 CUDA tensor of the same size; returns float64
+    (into `out` if given), asynchronous on the stream."""
+    import torch
+    if not (_is_torch(vp) and vp.is_cuda and vp.dtype == torch.float32 and vp.is_contiguous()):
+        raise ValueError("vp must be a contiguous float32 CUDA tensor")
+    n = vp.numel()
+    if grad_m.numel() != n:
+        raise ValueError("size mismatch")
+    if out is None:
+        out = torch.empty_like(grad_m)
+    _chk(lib().fdw_velocity_gradient(vp.data_ptr(), _cuda_f64(grad_m, "grad_m"), n,
+                                     _cuda_f64(out, "out"), _stream_handle(stream)))
+    return out
 
 
 class Closure:

@@ -127,8 +127,7 @@ class FwiTraces(torch.autograd.Function):
             gm += eng.adjoint_shot(k, grad_traces[k].double(), cks[k])
             cks[k] = None
         eng.close()
-        v = vp.detach().double()
-        gv = gm * (-2.0 / v ** 3)
+        gv = fdwave.velocity_gradient(vp.detach().float().contiguous(), gm)
         return gv.to(vp.dtype), None
 
 
@@ -154,5 +153,4 @@ def misfit_and_gradient(vp, survey: Survey, d_obs):
         gm += eng.adjoint_shot(k, res, ck)
         del ck
     eng.close()
-    v = vp.detach().double()
-    return J, (gm * (-2.0 / v ** 3)).to(vp.dtype)
+    return J, fdwave.velocity_gradient(vp.detach().float().contiguous(), gm).to(vp.dtype)

@@ -251,3 +251,19 @@ def test_full_size_gradient(fdw):
             fd[eps] = (J(v + eps * dvt) - J(v - eps * dvt)) / (2 * eps)
         rich = (4 * fd[0.25] - fd[0.5]) / 3
         assert abs(rich - lin) <= 3e-2 * abs(lin), (k, rich, lin)
+
+
+def test_velocity_gradient_chain_rule(fdw):
+    """fdw_velocity_gradient: dJ/dv = -2 v^-3 dJ/dm (m = 1/v^2) elementwise,
+    against the same rule in FP64 numpy, also when the output aliases the
+    input gradient."""
+    import torch
+    rng = np.random.default_rng(5)
+    v = rng.uniform(1500.0, 4500.0, size=(7, 9, 11)).astype(np.float32)
+    gm = rng.standard_normal(v.shape)
+    want = -2.0 * gm / v.astype(np.float64) ** 3
+    vt, gt = torch.from_numpy(v).cuda(), torch.from_numpy(gm).cuda()
+    got = fdw.velocity_gradient(vt, gt).cpu().numpy()
+    np.testing.assert_allclose(got, want, rtol=1e-15, atol=0)
+    fdw.velocity_gradient(vt, gt, out=gt)
+    np.testing.assert_allclose(gt.cpu().numpy(), want, rtol=1e-15, atol=0)
