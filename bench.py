@@ -482,7 +482,7 @@ def run_tti(args, stream, steps, warmup):
 def storage_errors():
     """Relative L2 errors against the FP64 oracle of FP32 / BF16 / FP16
     storage on reduced problems (acoustic 48^3 + 10 sponge, order 8, 150
-    steps; TTI 36^3 + 8 sponge, order 8, 100 steps), per field."""
+    steps; TTI 64^3 + 8 sponge, order 8, 150 steps), per field."""
     import numpy as np
     from oracle import oracle as O
     from paper_1608_03984_gb300 import fdwave, synth
@@ -501,7 +501,7 @@ def storage_errors():
         out["acoustic"][st] = {"traces": rel(s.traces(), ref["traces"]),
                                "u": rel(s.wavefield(0, 0), ref["u"])}
         s.close()
-    t = synth.random_tti(n=36, nb=8, order=8, nt=100, nrec_side=6)
+    t = synth.random_tti(n=64, nb=8, order=8, nt=150, nrec_side=8)
     ref = O.tti_forward(O.Setup(t.vp, t.h, t.nb, t.order, t.dt, eps=t.eps, delta=t.delta,
                                 theta=t.theta, phi=t.phi), t.src_xyz, t.wavelet, t.nt, t.rec_xyz)
     for st in ("f32", "bf16", "f16"):
@@ -512,7 +512,7 @@ def storage_errors():
                           "r": rel(s.wavefield(1, 0), ref["r"])}
         s.close()
     out["problems"] = ("acoustic two-layer 48^3 + 10 sponge, order 8, 150 steps; "
-                       "TTI random 36^3 + 8 sponge, order 8, 100 steps; relative L2 vs FP64 oracle")
+                       "TTI random 64^3 + 8 sponge, order 8, 150 steps; relative L2 vs FP64 oracle")
     return out
 
 
@@ -671,7 +671,8 @@ def run_closure(args):
             "speedup_vs_fine": {"coarse": ms["fine"] / ms["coarse"], "closure": ms["fine"] / ms["closure"]},
             "closure_ms_per_step": (ms["closure"] - ms["coarse"] * k1 / nt) / (nt - k1),
             "coarse_ms_per_step": ms["coarse"] / nt,
-            "inference": "tensor cores (mma.sync m16n8k16, FP16 operands, FP32 accumulation)",
+            "inference": "tcgen05.mma kind::f16 (M = 128 points, N = 48 / 32, K = 16; FP16 operands, FP32 "
+                         "accumulators in tensor memory)",
             "one_step_unexplained": unexpl, "train_loss_first_last": [losses[0], losses[-1]],
             "data_s": t1 - t0, "train_s": t2 - t1, "iters": args.closure_iters,
             "every_k_steps": sub,
@@ -713,6 +714,9 @@ def headline(full, details_path):
     if st:
         summ["storage_speedup_vs_f32"] = {o: {k: _r(v["speedup_vs_f32"]) for k, v in st[o].items()}
                                           for o in st if o.isdigit()}
+        er = st.get("errors_vs_fp64_oracle") or {}
+        summ["storage_error_vs_fp64"] = {eq: {sto: {f: _r(x, 3) for f, x in v.items()} for sto, v in er[eq].items()}
+                                         for eq in ("acoustic", "tti") if eq in er}
     fw = full.get("fwi")
     if fw:
         summ["fwi"] = {"gradient_s": _r(fw["gradient_s"]), "per_shot_s": _r(fw["per_shot_s"]),

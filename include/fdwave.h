@@ -91,8 +91,11 @@ int fdw_destroy(fdw_solver *s);
  * recommended for stability), theta (tilt) and phi (azimuth) in radians;
  * pass NULL for those with the acoustic equation. The sponge points take
  * the value of the nearest physical point. Invalidates dt (call
- * fdw_set_dt again). Errors: INVALID_ARG (NULL vp, vp <= 0 or non-finite
- * found on a host array), CUDA.
+ * fdw_set_dt again). With BF16/FP16 storage the TTI axis is stored as two
+ * components (nx, ny) and nz rebuilt, whose rounding error grows as the
+ * axis tips over: tilts beyond 75 degrees are rejected for 16-bit storage
+ * (FP32 storage takes any tilt). Errors: INVALID_ARG (NULL vp, vp <= 0 or
+ * non-finite, a tilt beyond 75 degrees with 16-bit TTI storage), CUDA.
  */
 int fdw_set_model(fdw_solver *s, const float *vp, const float *eps, const float *delta,
                   const float *theta, const float *phi, int ptr_is_device);
@@ -368,10 +371,12 @@ int fdw_closure_create(fdw_closure **out, void *stream);
 int fdw_closure_destroy(fdw_closure *c);
 
 /*
- * Inference kernels of fdw_step_closure: 0 (default) = one fused kernel on
- * the tensor cores (mma.sync, FP16 operands: the BF16 weights exactly, the
- * activations rounded to FP16; FP32 accumulation), 1 = plain FP32
- * convolutions on the CUDA cores (the cross-check). Errors: INVALID_ARG.
+ * Inference kernels of fdw_step_closure: 0 (default) = one persistent kernel
+ * on the Blackwell tensor cores (tcgen05.mma from shared memory into tensor
+ * memory), 2 = one fused kernel on warp-level tensor-core MMAs (mma.sync);
+ * both take FP16 operands (the BF16 weights exactly, the activations
+ * rounded to FP16) with FP32 accumulation; 1 = plain FP32 convolutions on
+ * the CUDA cores (the cross-check). Errors: INVALID_ARG.
  */
 int fdw_closure_set_variant(fdw_closure *c, int variant);
 

@@ -435,7 +435,7 @@ int closure_reserve_infer(ClosureNet *c, Dims d) {
   }
   if (!c->s_dev && cudaMalloc(&c->s_dev, sizeof(float)) != cudaSuccess) return -1;
   if (!c->s_partial && cudaMalloc(&c->s_partial, 1024 * sizeof(float)) != cudaSuccess) return -1;
-  if (c->variant == 0) return closure_tc_reserve(c, d);
+  if (c->variant != 1) return closure_tc_reserve(c, d);
   if (!c->x) {
     if (cudaMalloc(&c->x, 3 * vol * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&c->ia1, (size_t)kH * vol * sizeof(float)) != cudaSuccess ||
@@ -463,8 +463,8 @@ static cudaError_t infer_pre_t(ClosureNet *c, const T *u, const T *um, const flo
 }
 
 cudaError_t closure_infer_base(ClosureNet *c, const float *vp, int nx, int ny, int nz, int nb, Dims d,
-                               cudaStream_t st) {
-  if (c->variant == 0) return closure_tc_base(c, vp, nx, ny, nz, nb, d, st);
+                               int *err, cudaStream_t st) {
+  if (c->variant != 1) return closure_tc_base(c, vp, nx, ny, nz, nb, d, err, st);
   const long long vol = (long long)d.NX * d.NY * d.NZ;
   closure_inputs_kernel<float><<<grid_for(vol), 256, 0, st>>>(nullptr, nullptr, vp, nx, ny, nz, nb, d, c->s_dev,
                                                               c->x);
@@ -482,8 +482,8 @@ static void absmax_t(ClosureNet *c, const T *u, Dims d, cudaStream_t st) {
 }
 
 cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const void *um, const float *vp,
-                              int nx, int ny, int nz, int nb, Dims d, cudaStream_t st) {
-  if (c->variant == 0) {
+                              int nx, int ny, int nz, int nb, Dims d, int *err, cudaStream_t st) {
+  if (c->variant != 1) {
     switch (storage) {
       case FDW_F32: absmax_t(c, (const float *)u, d, st); break;
       case FDW_BF16: absmax_t(c, (const __nv_bfloat16 *)u, d, st); break;
@@ -492,7 +492,7 @@ cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const v
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return closure_tc_net(c, storage, u, um, vp, nx, ny, nz, nb, d, st);
+    return closure_tc_net(c, storage, u, um, vp, nx, ny, nz, nb, d, err, st);
   }
   switch (storage) {
     case FDW_F32: return infer_pre_t<float>(c, (const float *)u, (const float *)um, vp, nx, ny, nz, nb, d, st);
@@ -527,7 +527,7 @@ __global__ void closure_apply_out_kernel(const float *__restrict__ net, const fl
 cudaError_t closure_infer_apply(ClosureNet *c, int storage, void *unew, Dims d, int nx, int ny, int nz, int nb,
                                 float factor, cudaStream_t st) {
   const long long vol = (long long)d.NX * d.NY * d.NZ;
-  if (c->variant == 0) {
+  if (c->variant != 1) {
     switch (storage) {
       case FDW_F32:
         closure_apply_out_kernel<float><<<grid_for(vol), 256, 0, st>>>(c->tc_out, c->base, c->s_dev, (float *)unew,
@@ -684,13 +684,13 @@ extern "C" int fdw_closure_destroy(fdw_closure *c) {
   cudaFree(c->partial); cudaFree(c->loss_partial);
   cudaFree(c->xpair);
   cudaFree(c->x); cudaFree(c->ia1); cudaFree(c->ia2); cudaFree(c->base); cudaFree(c->s_dev); cudaFree(c->s_partial);
-  cudaFree(c->x16); cudaFree(c->tc_out); cudaFree(c->tcw);
+  cudaFree(c->x16); cudaFree(c->tc_out); cudaFree(c->tcw); cudaFree(c->umw);
   delete c;
   return FDW_OK;
 }
 
 extern "C" int fdw_closure_set_variant(fdw_closure *c, int variant) {
-  if (!c || variant < 0 || variant > 1) return report_error(FDW_ERR_INVALID_ARG, "variant must be 0 or 1");
+  if (!c || variant < 0 || variant > 2) return report_error(FDW_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
   c->variant = variant;
   return FDW_OK;
 }

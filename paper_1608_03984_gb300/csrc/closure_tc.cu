@@ -465,6 +465,7 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
 // ---------------------------------------------------------------------------
 int closure_tc_reserve(ClosureNet *c, Dims d) {
   const size_t vol = (size_t)d.NX * d.NY * d.NZ;
+  if (c->variant == 0 && closure_umma_reserve(c)) return -1;
   if (c->tc_cap >= vol && c->tcw) return 0;
   cudaFree(c->x16);
   cudaFree(c->tc_out);
@@ -489,19 +490,15 @@ int closure_tc_reserve(ClosureNet *c, Dims d) {
   return 0;
 }
 
-static int tc_grid_for(long long n) {
-  long long b = (n + 255) / 256;
-  return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
-}
-
 // net(x) on the grid into `dst` (FP32 dense [NZ][NY][NX]); u == null: x0.
+// Variant 0 runs the tcgen05 kernel, variant 2 the mma.sync kernel.
 template <typename T>
 static cudaError_t tc_net(ClosureNet *c, const T *u, const T *um, const float *vp, int nx, int ny, int nz, int nb,
-                          Dims d, float *dst, cudaStream_t st) {
-  const long long vol = (long long)d.NX * d.NY * d.NZ;
+                          Dims d, float *dst, int *err, cudaStream_t st) {
   const long rows = (long)d.NY * d.NZ;
   tc_inputs_kernel<T><<<(int)(rows < 152 * 64 ? rows : 152 * 64), 256, 0, st>>>(u, um, vp, nx, ny, nz, nb, d,
                                                                                 c->s_dev, (uint2 *)c->x16);
+  if (c->variant == 0) return closure_umma_run(c, c->x16, dst, d, err, st);
   const int tiles = ((d.NX + tc::TX - 1) / tc::TX) * ((d.NY + tc::TY - 1) / tc::TY);
   int zch = (2 * 152 + tiles - 1) / tiles;  // about two CTAs per SM in total
   if (zch < 1) zch = 1;
@@ -514,23 +511,29 @@ static cudaError_t tc_net(ClosureNet *c, const T *u, const T *um, const float *v
   return cudaGetLastError();
 }
 
-cudaError_t closure_tc_base(ClosureNet *c, const float *vp, int nx, int ny, int nz, int nb, Dims d,
+cudaError_t closure_tc_base(ClosureNet *c, const float *vp, int nx, int ny, int nz, int nb, Dims d, int *err,
                             cudaStream_t st) {
-  tc_prepare_kernel<<<1, 256, 0, st>>>(c->pb, c->pf, (TcWeights *)c->tcw);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (c->variant == 0) {
+    e = closure_umma_prepare(c, st);
+  } else {
+    tc_prepare_kernel<<<1, 256, 0, st>>>(c->pb, c->pf, (TcWeights *)c->tcw);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
-  return tc_net<float>(c, nullptr, nullptr, vp, nx, ny, nz, nb, d, c->base, st);
+  return tc_net<float>(c, nullptr, nullptr, vp, nx, ny, nz, nb, d, c->base, err, st);
 }
 
 cudaError_t closure_tc_net(ClosureNet *c, int storage, const void *u, const void *um, const float *vp, int nx,
-                           int ny, int nz, int nb, Dims d, cudaStream_t st) {
+                           int ny, int nz, int nb, Dims d, int *err, cudaStream_t st) {
   switch (storage) {
-    case FDW_F32: return tc_net<float>(c, (const float *)u, (const float *)um, vp, nx, ny, nz, nb, d, c->tc_out, st);
+    case FDW_F32:
+      return tc_net<float>(c, (const float *)u, (const float *)um, vp, nx, ny, nz, nb, d, c->tc_out, err, st);
     case FDW_BF16:
       return tc_net<__nv_bfloat16>(c, (const __nv_bfloat16 *)u, (const __nv_bfloat16 *)um, vp, nx, ny, nz, nb, d,
-                                   c->tc_out, st);
+                                   c->tc_out, err, st);
     case FDW_F16:
-      return tc_net<__half>(c, (const __half *)u, (const __half *)um, vp, nx, ny, nz, nb, d, c->tc_out, st);
+      return tc_net<__half>(c, (const __half *)u, (const __half *)um, vp, nx, ny, nz, nb, d, c->tc_out, err, st);
     default: return cudaErrorInvalidValue;
   }
 }

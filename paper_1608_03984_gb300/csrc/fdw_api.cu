@@ -585,8 +585,9 @@ extern "C" int fdw_set_model(fdw_solver *s, const float *vp, const float *eps, c
     CK(cudaMemcpyAsync(s->theta, theta, n * sizeof(float), k, s->stream));
     CK(cudaMemcpyAsync(s->phi, phi, n * sizeof(float), k, s->stream));
   }
-  CK(launch_max_velocity(s->vp, tti ? s->eps : nullptr, (long)n, s->scratch2, s->stream));
-  float vm[3];
+  CK(launch_max_velocity(s->vp, tti ? s->eps : nullptr, tti ? s->theta : nullptr, (long)n, s->scratch2,
+                         s->stream));
+  float vm[4];
   CK(cudaMemcpyAsync(vm, s->scratch2, sizeof vm, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   int bad;
@@ -595,6 +596,19 @@ extern "C" int fdw_set_model(fdw_solver *s, const float *vp, const float *eps, c
     s->model_set = false;
     s->dt_set = false;
     return fail(FDW_ERR_INVALID_ARG, "vp must be positive and finite everywhere (max %g)", (double)vm[0]);
+  }
+  // 16-bit storage keeps the axis as (nx, ny) and rebuilds nz = sqrt(1 -
+  // nx^2 - ny^2): the rounding of nx, ny enters the cross coefficients
+  // nx nz, ny nz amplified by about 1 / (2 nz), so beyond 75 degrees of tilt
+  // (1 / (2 cos 75) ~ 2) the rebuilt axis is no longer at the storage's own
+  // precision: such models need FP32 storage.
+  if (tti && s->storage != FDW_F32 && vm[3] > 1.f - 0.258819045f) {
+    s->model_set = false;
+    s->dt_set = false;
+    return fail(FDW_ERR_INVALID_ARG,
+                "tilt up to %.1f degrees: 16-bit storage of the TTI axis is limited to 75 degrees "
+                "(use FP32 storage)",
+                acos(1.0 - (double)vm[3]) * 180.0 / M_PI);
   }
   s->vmax = vm[0];
   s->vmax_eff = vm[1];
@@ -1148,7 +1162,7 @@ extern "C" int fdw_step_closure_every(fdw_solver *s, fdw_closure *c, int nsteps,
   CK(acoustic_prepare(s->storage, s->r, s->tile));
   if (closure_reserve_infer(c, s->d)) return fail(FDW_ERR_OOM, "closure inference workspace");
   if (nsteps > 0)  // the network's answer for a zero wavefield, subtracted every step
-    CK(closure_infer_base(c, s->vp, s->nx, s->ny, s->nz, s->nb, s->d, s->stream));
+    CK(closure_infer_base(c, s->vp, s->nx, s->ny, s->nz, s->nb, s->d, s->d_err, s->stream));
   const size_t fb = s->d.vol() * s->el;
   for (int n = 0; n < nsteps; ++n) {
     const int cur = s->cur, nxt = 1 - cur;
@@ -1157,7 +1171,7 @@ extern "C" int fdw_step_closure_every(fdw_solver *s, fdw_closure *c, int nsteps,
     const bool corr = ((s->it + n) % every) == 0;
     if (corr)
       CK(closure_infer_pre(c, s->storage, s->f[0][cur], s->f[0][nxt], s->vp, s->nx, s->ny, s->nz, s->nb,
-                           s->d, s->stream));
+                           s->d, s->d_err, s->stream));
     rc = enqueue_stencil(s, cur, s->stream);
     if (rc) return rc;
     if (corr)

@@ -196,20 +196,24 @@ struct ClosureNet {
   size_t xcap = 0;                // floats in xpair
   // inference workspace (one computational grid); base = net(0, 0, v)
   float *x = nullptr, *ia1 = nullptr, *ia2 = nullptr, *base = nullptr, *s_dev = nullptr;
-  // tensor-core inference (closure_tc.cu): FP16 inputs, network output, weights
-  void *x16 = nullptr, *tcw = nullptr;
+  // tensor-core inference (closure_tc.cu, closure_umma.cu): FP16 inputs,
+  // network output, operands of the mma.sync and tcgen05 kernels
+  void *x16 = nullptr, *tcw = nullptr, *umw = nullptr;
   float *tc_out = nullptr;
   size_t tc_cap = 0;
-  int variant = 0;                // 0: tensor-core kernel, 1: FP32 CUDA-core kernels
+  // 0: tcgen05 kernel (closure_umma.cu), 1: FP32 CUDA-core kernels,
+  // 2: mma.sync kernel (closure_tc.cu)
+  int variant = 0;
   float *s_partial = nullptr;     // per-block maxima of |u_n|
   size_t infer_cap = 0;           // points
 };
-// Once per fdw_step_closure call: base = net(0, 0, v) on the grid.
+// Once per fdw_step_closure call: base = net(0, 0, v) on the grid. `err`
+// receives device-side wait timeouts (tcgen05 kernel).
 cudaError_t closure_infer_base(ClosureNet *c, const float *vp, int nx, int ny, int nz, int nb, Dims d,
-                               cudaStream_t st);
+                               int *err, cudaStream_t st);
 // Before the stencil of a step: s = max |u_n|, inputs, the first two layers.
 cudaError_t closure_infer_pre(ClosureNet *c, int storage, const void *u, const void *um,
-                              const float *vp, int nx, int ny, int nz, int nb, Dims d,
+                              const float *vp, int nx, int ny, int nz, int nb, Dims d, int *err,
                               cudaStream_t st);
 // After the stencil: u_{n+1} += factor * s * (last layer - base) on the
 // physical points (sponge width nb, physical extents nx, ny, nz).
@@ -219,9 +223,14 @@ int closure_reserve_infer(ClosureNet *c, Dims d);
 // tensor-core path (closure_tc.cu)
 int closure_tc_reserve(ClosureNet *c, Dims d);
 cudaError_t closure_tc_base(ClosureNet *c, const float *vp, int nx, int ny, int nz, int nb, Dims d,
-                            cudaStream_t st);
+                            int *err, cudaStream_t st);
 cudaError_t closure_tc_net(ClosureNet *c, int storage, const void *u, const void *um, const float *vp, int nx,
-                           int ny, int nz, int nb, Dims d, cudaStream_t st);
+                           int ny, int nz, int nb, Dims d, int *err, cudaStream_t st);
+// tcgen05 path (closure_umma.cu): operand buffer, operand preparation, the
+// network on the FP16 inputs x16 into dst (FP32, dense [NZ][NY][NX])
+int closure_umma_reserve(ClosureNet *c);
+cudaError_t closure_umma_prepare(ClosureNet *c, cudaStream_t st);
+cudaError_t closure_umma_run(ClosureNet *c, const void *x16, float *dst, Dims d, int *err, cudaStream_t st);
 
 }  // namespace fdw
 
@@ -244,7 +253,7 @@ cudaError_t launch_coef_tti(int storage, const float *vp, const float *eps, cons
                             const float *theta, const float *phi, int nx, int ny, int nz,
                             int nb, Dims d, double dt_over_h, void *c, void *e, void *dl,
                             void *ax, void *ay, cudaStream_t st);
-cudaError_t launch_max_velocity(const float *vp, const float *eps, long n, float *out3,
+cudaError_t launch_max_velocity(const float *vp, const float *eps, const float *theta, long n, float *out4,
                                 cudaStream_t st);
 // dense [NZ][NY][NX] f32 <-> padded storage, values multiplied by `scale`
 cudaError_t launch_pack(int storage, const float *src, void *dst, Dims d, float scale,

@@ -74,25 +74,31 @@ __global__ void coef_tti_kernel(const float *__restrict__ vp, const float *__res
   }
 }
 
+// out[0] = max v, out[1] = max v sqrt(1 + 2 eps), out[2] = flag of a
+// non-positive or non-finite v, out[3] = max (1 - |cos theta|) (steepest
+// tilt); out must be zeroed (all maxima are of non-negative values).
 __global__ void max_velocity_kernel(const float *__restrict__ vp, const float *__restrict__ eps,
-                                    long n, float *out) {
-  float m0 = 0.f, m1 = 0.f;
+                                    const float *__restrict__ theta, long n, float *out) {
+  float m0 = 0.f, m1 = 0.f, m3 = 0.f;
   int bad = 0;
   for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
     const float v = vp[p];
     bad |= !(v > 0.f) || !isfinite(v);
     m0 = fmaxf(m0, v);
     m1 = fmaxf(m1, eps ? v * sqrtf(1.f + 2.f * eps[p]) : v);
+    if (theta) m3 = fmaxf(m3, 1.f - fabsf(cosf(theta[p])));
   }
   for (int o = 16; o > 0; o >>= 1) {
     m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
     m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+    m3 = fmaxf(m3, __shfl_xor_sync(0xffffffffu, m3, o));
     bad |= __shfl_xor_sync(0xffffffffu, bad, o);
   }
   if ((threadIdx.x & 31) == 0) {
     atomicMax((int *)&out[0], __float_as_int(m0));
     atomicMax((int *)&out[1], __float_as_int(m1));
     if (bad) atomicOr((int *)&out[2], 1);
+    atomicMax((int *)&out[3], __float_as_int(m3));
   }
 }
 
@@ -157,11 +163,11 @@ cudaError_t launch_coef_tti(int storage, const float *vp, const float *eps, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_max_velocity(const float *vp, const float *eps, long n, float *out3,
+cudaError_t launch_max_velocity(const float *vp, const float *eps, const float *theta, long n, float *out4,
                                 cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(out3, 0, 3 * sizeof(float), st);
+  cudaError_t e = cudaMemsetAsync(out4, 0, 4 * sizeof(float), st);
   if (e != cudaSuccess) return e;
-  max_velocity_kernel<<<grid_for((size_t)n), 256, 0, st>>>(vp, eps, n, out3);
+  max_velocity_kernel<<<grid_for((size_t)n), 256, 0, st>>>(vp, eps, theta, n, out4);
   return cudaGetLastError();
 }
 

@@ -225,8 +225,9 @@ class Closure:
             pass
 
     def set_variant(self, variant):
-        """Inference kernels of Solver.step_closure: 0 tensor cores (default),
-        1 FP32 CUDA-core convolutions."""
+        """Inference kernels of Solver.step_closure: 0 tcgen05 tensor-core
+        kernel (default), 1 FP32 CUDA-core convolutions, 2 mma.sync
+        tensor-core kernel."""
         _chk(lib().fdw_closure_set_variant(self._h, int(variant)))
 
     def set_params(self, p):

@@ -91,7 +91,10 @@ def _full_result():
         "storage": dict({o: {st: {"kernel_ms": 0.4, "gpts": 500.0, "speedup_vs_f32": 1.2345,
                                   "achieved_gbs": 4000.0, "frac_of_measured_hbm": 0.6}
                              for st in ("bf16", "f16")} for o in orders},
-                        errors_vs_fp64_oracle={"acoustic": {}, "tti": {}, "problems": "x" * 200}),
+                        errors_vs_fp64_oracle={
+                            "acoustic": {st: {"traces": 0.0161234, "u": 0.029} for st in ("f32", "bf16", "f16")},
+                            "tti": {st: {"traces": 0.011, "p": 0.069, "r": 0.082} for st in ("f32", "bf16", "f16")},
+                            "problems": "x" * 200}),
         "fwi": {"workload": "fwi 256^3", "gradient_s": 19.01, "per_shot_s": 1.19, "shots": 16, "misfit": 1.0,
                 "stencil_steps": 96000, "gpts_equiv": 190.0, "gradient_finite": True},
         "closure": {"error_vs_fine": {"coarse": {"field": 0.0448, "traces": 0.0178},
@@ -121,7 +124,9 @@ def test_headline_line_is_compact_and_complete():
     assert line["value"] > 0 and line["roofline"]["frac"] > 0
     assert "note" not in line["e2e"] and line["e2e"]["h2d_bytes_per_step"] > 0
     assert set(line["per_order"]) == set(full["per_order"])
-    assert set(line["sections"]) == {"tti", "storage_speedup_vs_f32", "fwi", "closure", "config1"}
+    assert set(line["sections"]) == {"tti", "storage_speedup_vs_f32", "storage_error_vs_fp64", "fwi", "closure",
+                                     "config1"}
+    assert line["sections"]["storage_error_vs_fp64"]["tti"]["bf16"]["p"] == 0.069
     assert line["sections"]["closure"]["operating_point"]["every"] == 4
     assert line["details"] == "bench_details.json"
     # sections that did not run are simply absent

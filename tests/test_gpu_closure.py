@@ -289,7 +289,7 @@ def test_step_closure_16bit_storage(fdw, O, storage):
     solver.close()
 
 
-def _tc_vs_oracle_correction(fdw, O, seed, pscale):
+def _tc_vs_oracle_correction(fdw, O, seed, pscale, variant=0):
     """(GPU correction, oracle correction) of one closure step from random
     levels: the closure step's u_{n+1} minus the plain step's (the source
     term cancels)."""
@@ -297,6 +297,7 @@ def _tc_vs_oracle_correction(fdw, O, seed, pscale):
     plain, *_ = _coarse_case(fdw, O, seed)
     p = random_params(seed, scale=pscale)
     net = fdw.Closure()
+    net.set_variant(variant)
     net.set_params(p)
     solver.step_closure(net, 1)
     plain.step(1)
@@ -309,24 +310,28 @@ def _tc_vs_oracle_correction(fdw, O, seed, pscale):
     return got, ref
 
 
+@pytest.mark.parametrize("variant", [0, 2])
 @pytest.mark.parametrize("seed", [61, 62])
-def test_tensor_core_step_matches_oracle(fdw, O, seed):
-    """The fused tensor-core inference (FP16 operands, FP32 accumulation)
-    against the oracle's FP64 closure step: the correction agrees to the
-    FP16 rounding of the activations. Bound: each activation carries a
-    relative rounding error <= 2^-11; through two layers of 432-term sums
-    the correction's relative L2 error stays well below 1e-2."""
-    got, ref = _tc_vs_oracle_correction(fdw, O, seed, 0.3)
+def test_tensor_core_step_matches_oracle(fdw, O, seed, variant):
+    """The fused tensor-core inference (FP16 operands, FP32 accumulation;
+    tcgen05 and mma.sync kernels) against the oracle's FP64 closure step:
+    the correction agrees to the FP16 rounding of the activations. Bound:
+    each activation carries a relative rounding error <= 2^-11; through two
+    layers of 432-term sums the correction's relative L2 error stays well
+    below 1e-2."""
+    got, ref = _tc_vs_oracle_correction(fdw, O, seed, 0.3, variant)
     assert np.linalg.norm(ref) > 0
     assert rel(got, ref) < 1e-2
 
 
-def test_tensor_core_matches_fp32_kernels(fdw, O):
+@pytest.mark.parametrize("variant", [0, 2])
+def test_tensor_core_matches_fp32_kernels(fdw, O, variant):
     """Tensor-core and FP32 inference kernels on the same state: the
     corrections agree to FP16 rounding (the grid, 32 x 34 x 36 with the
-    sponge, is ragged for the 30 x 14 tile and split in two z chunks)."""
+    sponge, is ragged for both kernels' tiles -- 12 x 28 for tcgen05,
+    30 x 14 for mma.sync -- and split into z chunks)."""
     corr = []
-    for variant in (0, 1):
+    for variant in (variant, 1):
         solver, *_ = _coarse_case(fdw, O, 71)
         plain, *_ = _coarse_case(fdw, O, 71)
         net = fdw.Closure()

@@ -137,3 +137,23 @@ def test_full_size_sampled_step_16bit(fdw, O, storage, order):
     tol = {"bf16": 2.5e-2, "f16": 3e-3}[storage]
     assert worst < tol, worst
     s.close()
+
+
+def test_16bit_tti_rejects_steep_tilts(fdw):
+    """16-bit storage keeps the TTI axis as (nx, ny) and rebuilds nz; beyond
+    75 degrees of tilt that loses the storage's precision, so such models are
+    rejected for BF16/FP16 and accepted in FP32."""
+    from paper_1608_03984_gb300 import synth
+    t = synth.random_tti(n=12, nb=2, order=4, nt=2, nrec_side=2)
+    steep = t.theta.copy()
+    steep[5, 5, 5] = np.deg2rad(80.0)
+    for st in ("bf16", "f16"):
+        s = fdw.Solver(t.n, t.h, t.nb, t.order, equation="tti", storage=st)
+        s.set_model(t.vp, t.eps, t.delta, t.theta, t.phi)  # <= 60 degrees: accepted
+        with pytest.raises(fdw.FdwError) as e:
+            s.set_model(t.vp, t.eps, t.delta, steep, t.phi)
+        assert e.value.code == -1 and "75 degrees" in str(e.value)
+        s.close()
+    s = fdw.Solver(t.n, t.h, t.nb, t.order, equation="tti", storage="f32")
+    s.set_model(t.vp, t.eps, t.delta, steep, t.phi).set_dt(t.dt)
+    s.close()
