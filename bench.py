@@ -591,6 +591,9 @@ def operating_point(field_err_1, ms, sub):
         e = sub[k]["error_vs_fine"]["field"]
         if e <= 1.05 * field_err_1 and int(k) > best["every"]:
             best = {"every": int(k), "field_error": e, "speedup_vs_fine": sub[k]["speedup_vs_fine"]}
+    # k is picked on the same models whose errors are reported (no separate
+    # validation set): the reported error at k is that selection's
+    best["selected_on"] = "evaluation models"
     return best
 
 
@@ -726,7 +729,8 @@ def headline(full, details_path):
         summ["closure"] = {
             "field_error_vs_fine": {m: _r(v["field"]) for m, v in cl["error_vs_fine"].items()},
             "speedup_vs_fine_every_step": _r(cl["speedup_vs_fine"]["closure"]),
-            "operating_point": {k: _r(v) for k, v in cl["operating_point"].items()}}
+            "operating_point": {k: (_r(v) if not isinstance(v, str) else v)
+                                for k, v in cl["operating_point"].items()}}
     c1 = full.get("config1")
     if c1:
         summ["config1"] = {"gpts": _r(c1["gpts"]), "ms_per_run": _r(c1["ms_per_run"])}

@@ -50,7 +50,7 @@ def test_closure_operating_point():
            "4": {"error_vs_fine": {"field": 0.0104}, "speedup_vs_fine": 3.4},
            "8": {"error_vs_fine": {"field": 0.0300}, "speedup_vs_fine": 5.6}}
     op = bench.operating_point(0.0100, ms, sub)
-    assert op == {"every": 4, "field_error": 0.0104, "speedup_vs_fine": 3.4}
+    assert op == {"every": 4, "field_error": 0.0104, "speedup_vs_fine": 3.4, "selected_on": "evaluation models"}
     bad = {k: {"error_vs_fine": {"field": 0.05}, "speedup_vs_fine": 9.0} for k in ("2", "4")}
     assert bench.operating_point(0.0100, ms, bad)["every"] == 1
 
@@ -100,7 +100,8 @@ def _full_result():
         "closure": {"error_vs_fine": {"coarse": {"field": 0.0448, "traces": 0.0178},
                                       "closure": {"field": 0.0145, "traces": 0.0190}},
                     "speedup_vs_fine": {"coarse": 16.4, "closure": 1.01},
-                    "operating_point": {"every": 4, "field_error": 0.01451234, "speedup_vs_fine": 3.4212},
+                    "operating_point": {"every": 4, "field_error": 0.01451234, "speedup_vs_fine": 3.4212,
+                                        "selected_on": "evaluation models"},
                     "per_model": per_model, "every_k_steps": {str(k): {"x": 1} for k in (2, 4, 8, 16)}},
         "config1": {"workload": "two_layer 64^3", "ms_per_run": 2.5, "us_per_step": 12.5, "gpts": 47.4},
         "paper_model_gb300": {"table_cost": {str(o): {"I_alg": 1.0} for o in range(2, 26, 2)}},
