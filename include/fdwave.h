@@ -212,7 +212,7 @@ int fdw_set_zchunks(fdw_solver *s, int zchunks);
 /*
  * Tile configuration of the 2.5D kernel: acoustic (points per thread in x/y,
  * warps per CTA, z unrolling, planes per CTA barrier; acoustic_kernel.cuh)
- * or TTI (warps per CTA, z unrolling; tti_kernel.cuh): acoustic 0..11, TTI
+ * or TTI (warps per CTA, z unrolling; tti_kernel.cuh): acoustic 0..12, TTI
  * 0..8, or -1 for the default of the solver's equation, order and storage.
  * Resets zchunks to its default.
  * fdw_get_tile_config returns the configuration in use (-1 for NULL).

@@ -399,7 +399,8 @@ void tile_cfg(TileGeom *g) {
   X(8, 4, 1, 8, 4, 2, 4)  \
   X(9, 4, 2, 4, 4, 2, 3)  \
   X(10, 4, 2, 4, 4, 1, 3) \
-  X(11, 2, 2, 8, 4, 2, 3)
+  X(11, 2, 2, 8, 4, 2, 3) \
+  X(12, 4, 2, 4, 2, 2, 4)
 
 // Per-storage dispatch over radius and configuration (one TU per storage).
 #define FDW_AC_DEFINE_STORAGE(SUFFIX, TYPE)                                                   \

@@ -95,7 +95,7 @@ struct TileGeom {
   int box_halo_x, box_halo_y, box_int_x, box_int_y, smem;
 };
 constexpr int kGraphSteps = 16;  // steps per CUDA graph of a long fdw_step run (even)
-constexpr int kAcTiles = 12;  // number of configurations (see acoustic_kernel.cuh)
+constexpr int kAcTiles = 13;  // number of configurations (see acoustic_kernel.cuh)
 // 0 on success, -1 for an unknown (storage, r, tile).
 int acoustic_geom(int storage, int r, int tile, TileGeom *g);
 // Default configuration for (storage, r).

@@ -38,6 +38,15 @@ __global__ void coef_acoustic_kernel(const float *__restrict__ vp, int nx, int n
   }
 }
 
+// The next smaller value of a positive finite number of the storage type.
+__device__ __forceinline__ float ulp_down(float v) { return __uint_as_float(__float_as_uint(v) - 1u); }
+__device__ __forceinline__ __nv_bfloat16 ulp_down(__nv_bfloat16 v) {
+  return __ushort_as_bfloat16((unsigned short)(__bfloat16_as_ushort(v) - 1u));
+}
+__device__ __forceinline__ __half ulp_down(__half v) {
+  return __ushort_as_half((unsigned short)(__half_as_ushort(v) - 1u));
+}
+
 template <typename T>
 __global__ void coef_tti_kernel(const float *__restrict__ vp, const float *__restrict__ eps,
                                 const float *__restrict__ delta, const float *__restrict__ theta,
@@ -66,8 +75,18 @@ __global__ void coef_tti_kernel(const float *__restrict__ vp, const float *__res
         vy = sy;
       }
       c[p] = St<T>::st(vc);
-      e[p] = St<T>::st(ve);
-      dl[p] = St<T>::st(vd);
+      // The rounded pair must keep the system matrix [[e, d], [d, 1]] of
+      // Eq. TTI positive semidefinite (e >= d^2, i.e. eps >= delta, which
+      // the model may meet with equality): rounding e and d independently
+      // can give d^2 > e by an ulp of the storage type -- a local
+      // instability that 16-bit storage turns into growth. d is moved down
+      // by ulps until e >= d^2 holds exactly for the stored values.
+      const T es = St<T>::st(ve);
+      T ds = St<T>::st(vd);
+      for (int it = 0; it < 8 && (double)St<T>::ld(ds) * (double)St<T>::ld(ds) > (double)St<T>::ld(es); ++it)
+        ds = ulp_down(ds);
+      e[p] = es;
+      dl[p] = ds;
       ax[p] = St<T>::st(vx);
       ay[p] = St<T>::st(vy);
     }

@@ -283,7 +283,7 @@ def test_profiled_steps_match_graph_steps(fdw):
 
 
 @pytest.mark.parametrize("order", [2, 6, 8, 12, 16])
-@pytest.mark.parametrize("tile", list(range(12)))
+@pytest.mark.parametrize("tile", list(range(13)))
 def test_every_tile_configuration(fdw, O, order, tile):
     """Each tile configuration of the 2.5D kernel (points per thread, warps
     per CTA, z unrolling) reproduces the oracle's step on a grid with ragged
@@ -307,7 +307,7 @@ def test_every_tile_configuration(fdw, O, order, tile):
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
-@pytest.mark.parametrize("tile", list(range(1, 12)))
+@pytest.mark.parametrize("tile", list(range(1, 13)))
 def test_16bit_tile_configurations(fdw, storage, tile):
     """With 16-bit storage every tile configuration gives the fields of
     configuration 0 (one point per thread) up to one rounding of the stored

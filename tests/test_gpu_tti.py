@@ -196,3 +196,58 @@ def test_full_size_sampled_step(fdw, O, order):
         worst = max(worst, abs(float(pp[k, j, i]) - ep) / scale, abs(float(rp[k, j, i]) - er) / scale)
     assert worst < 1e-5, worst
     s.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_full_size_sampled_step_16bit(fdw, O, storage):
+    """The 464^3 TTI workload with 16-bit storage (order 8, the benchmark's
+    launch configuration): one step from random p, r levels, checked at
+    sampled points by the oracle's FP64 TTI point update of the stored
+    (rounded) input levels with the exact medium. The bound covers one
+    rounding of the stored output and the rounding of the stored medium
+    (c, 1 + 2 eps, sqrt(1 + 2 delta), the axis): a few units of 2^-9 (BF16)
+    or 2^-12 (FP16) of the largest input, the operator terms being up to
+    ~10 times that input at CFL 0.4."""
+    import torch
+    w = synth.random_tti(n=384, nb=40, order=8, nt=8, nrec_side=16)
+    s = tti_solver(fdw, w, storage)
+    comp = s.comp_shape
+    g = torch.Generator(device="cuda").manual_seed(987)
+    for f in (0, 1):
+        for lvl in (0, 1):
+            s.set_wavefield(1e-3 * torch.randn(comp, generator=g, device="cuda", dtype=torch.float32), f, lvl)
+    lv = [torch.empty(comp, device="cuda", dtype=torch.float32) for _ in range(4)]
+    for (f, lvl), a in zip([(0, 0), (0, 1), (1, 0), (1, 1)], lv):
+        s.wavefield(f, lvl, out=a)  # the stored values, as the kernel reads them
+    s.set_current_step(3)
+    s.set_sources(np.zeros((0, 3)), None)
+    s.step(1)
+    pp = torch.empty_like(lv[0])
+    rp = torch.empty_like(lv[0])
+    s.wavefield(0, 0, out=pp)
+    s.wavefield(1, 0, out=rp)
+    s.check()
+    torch.cuda.synchronize()
+    r = w.order // 2
+    rng = np.random.default_rng(2)
+    N = np.array(comp)
+    pts = [tuple(int(v) for v in rng.integers(0, N)) for _ in range(30)]
+    pts += [(0, 0, 0), tuple(int(v) for v in N - 1), (int(N[0]) // 2, int(N[1]) // 2, int(N[2]) // 2),
+            (39, 40, 41), (40, 40, 40)]
+    setup = tti_setup(O, w)
+    pad = [torch.nn.functional.pad(a.view(1, 1, *comp), (r,) * 6)[0, 0] for a in (lv[0], lv[2])]
+    worst = 0.0
+    for (k, j, i) in pts:
+        sl = (slice(k, k + 2 * r + 1), slice(j, j + 2 * r + 1), slice(i, i + 2 * r + 1))
+        pb, rb = (a[sl].double().cpu().numpy() for a in pad)
+        v_c = float(np.sqrt(setup.c[k, j, i])) / w.dt
+        gam = setup.gx[i] + setup.gy[j] + setup.gz[k]
+        ep, er = O.tti_update_at(pb, float(lv[1][k, j, i]), rb, float(lv[3][k, j, i]), v_c,
+                                 setup.eps[k, j, i], setup.delta[k, j, i], setup.theta[k, j, i],
+                                 setup.phi[k, j, i], gam, w.h, w.order, w.dt)
+        scale = max(np.abs(pb).max(), np.abs(rb).max())
+        worst = max(worst, abs(float(pp[k, j, i]) - ep) / scale, abs(float(rp[k, j, i]) - er) / scale)
+    tol = {"bf16": 5e-2, "f16": 6e-3}[storage]
+    assert worst < tol, worst
+    print("worst relative deviation (%s): %.3g" % (storage, worst))
+    s.close()
