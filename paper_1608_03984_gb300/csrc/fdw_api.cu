@@ -267,8 +267,9 @@ int min_zchunks(const fdw_solver *s) { return (s->d.NZ + kMaxZChunk - 1) / kMaxZ
 // plane iterations (the queue fill) and the grid runs in waves of (SMs x
 // resident CTAs per SM); the time is modelled as
 //   ceil(CTAs / slots) x (ceil(NZ / chunks) + 2r)
-// and minimised over the chunk counts that keep at least max(16, 4r)
-// planes per chunk: this picks the measured best chunking at every order.
+// and minimised over the chunk counts that keep at least max(4, r) planes
+// per chunk: this picks the measured best chunking at every order of the
+// 592^3 workload, and many short chunks on grids that fit in one wave.
 // The TTI kernel and the 16-bit acoustic kernels (more resident CTAs, short
 // fills) run best with more, smaller chunks: about 16 (TTI) or 32 (16-bit
 // acoustic) CTAs per SM in total.
@@ -278,7 +279,9 @@ int default_zchunks(const fdw_solver *s) {
   const int bad = tti ? tti_geom(s->storage, s->r, s->tile, &tg) : acoustic_geom(s->storage, s->r, s->tile, &tg);
   if (bad) return 1;
   const long tiles = (long)((s->d.NX + tg.box_int_x - 1) / tg.box_int_x) * ((s->d.NY + tg.box_int_y - 1) / tg.box_int_y);
-  const int zmin = 4 * s->r > 16 ? 4 * s->r : 16;
+  // chunks of at least 4 planes (and r): on small grids that fit in one
+  // wave, shorter chunks shorten every CTA's serial march
+  const int zmin = s->r > 4 ? s->r : 4;
   long maxch = s->d.NZ / zmin;
   if (maxch < 1) maxch = 1;
   const int lo = min_zchunks(s);

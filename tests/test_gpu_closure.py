@@ -465,3 +465,43 @@ def test_tensor_core_full_size_sampled(fdw, O):
     band = np.ones(comp, bool)
     band[a:N - a, a:N - a, a:N - a] = False
     assert np.all(corr[band] == 0.0)
+
+
+@pytest.mark.parametrize("shape,nb", [((9, 11, 13), 2), ((17, 30, 7), 3), ((40, 6, 29), 2)])
+def test_tcgen05_inference_ragged_grids(fdw, O, shape, nb):
+    """The tcgen05 kernel on grids that are not multiples of its 12 x 28
+    output column, thinner than the z halo of the three layers, or a single
+    work item: the correction of one closure step agrees with the FP32
+    CUDA-core kernels to FP16 rounding, and is exactly zero where the
+    receptive field leaves the physical grid."""
+    from paper_1608_03984_gb300 import synth
+    h, order = 20.0, 4
+    vp = synth.random_velocity(shape, h, 120.0, 300 + shape[0])
+    corr = []
+    for variant in (0, 1):
+        s = fdw.Solver(vp.shape, h, nb, order)
+        s.set_model(vp).set_sponge(4500.0).set_dt(0.35 * h / 4500.0)
+        pl = fdw.Solver(vp.shape, h, nb, order)
+        pl.set_model(vp).set_sponge(4500.0).set_dt(0.35 * h / 4500.0)
+        comp = s.comp_shape
+        u = synth.random_wavefield(comp, 11, smooth_pts=1.5).astype(np.float32)
+        um = synth.random_wavefield(comp, 12, smooth_pts=1.5).astype(np.float32)
+        for q in (s, pl):
+            q.set_wavefield(u, 0, 0)
+            q.set_wavefield(um, 0, 1)
+        net = fdw.Closure()
+        net.set_variant(variant)
+        net.set_params(random_params(13, scale=0.3))
+        s.step_closure(net, 1)
+        pl.step(1)
+        s.check()
+        corr.append(s.wavefield(0, 0).astype(np.float64) - pl.wavefield(0, 0))
+        net.close()
+        s.close()
+        pl.close()
+    if np.linalg.norm(corr[1]) > 0:
+        assert rel(corr[0], corr[1]) < 1e-2
+    m = np.zeros(corr[0].shape, bool)
+    a = nb + 3
+    m[a:-a or None, a:-a or None, a:-a or None] = True
+    assert np.all(corr[0][~m] == 0.0)
