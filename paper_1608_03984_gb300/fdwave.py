@@ -435,7 +435,7 @@ class Solver:
         _chk(lib().fdw_set_zchunks(self._h, int(zchunks)))
 
     def set_tile_config(self, tile):
-        """Tile configuration of the 2.5D kernel (acoustic 0..5, TTI 0..8), -1 = default."""
+        """Tile configuration of the 2.5D kernel (acoustic 0..12, TTI 0..8), -1 = default."""
         _chk(lib().fdw_set_tile_config(self._h, int(tile)))
 
     @property
