@@ -212,8 +212,9 @@ int fdw_set_zchunks(fdw_solver *s, int zchunks);
 /*
  * Tile configuration of the 2.5D kernel: acoustic (points per thread in x/y,
  * warps per CTA, z unrolling, planes per CTA barrier; acoustic_kernel.cuh)
- * or TTI (warps per CTA, z unrolling; tti_kernel.cuh): acoustic 0..12, TTI
- * 0..8, or -1 for the default of the solver's equation, order and storage.
+ * or TTI (warps per CTA, z unrolling, rows per thread; tti_kernel.cuh):
+ * acoustic 0..12, TTI 0..12 (9..12, two rows per thread, up to order 8),
+ * or -1 for the default of the solver's equation, order and storage.
  * Resets zchunks to its default.
  * fdw_get_tile_config returns the configuration in use (-1 for NULL).
  * Errors: INVALID_ARG.

@@ -262,17 +262,17 @@ void drop_graphs(fdw_solver *s) {
 int min_zchunks(const fdw_solver *s) { return (s->d.NZ + kMaxZChunk - 1) / kMaxZChunk; }
 
 // Default number of z chunks of the 2.5D kernels (measured on the 592^3
-// acoustic and 464^3 TTI workloads).
-// FP32 acoustic kernel: a CTA marching a chunk of L planes does L + 2r
-// plane iterations (the queue fill) and the grid runs in waves of (SMs x
-// resident CTAs per SM); the time is modelled as
+// acoustic and the 464^3 and 212^3 TTI workloads).
+// FP32 acoustic and TTI kernels: a CTA marching a chunk of L planes does
+// L + 2r plane iterations (the queue fill) and the grid runs in waves of
+// (SMs x resident CTAs per SM); the time is modelled as
 //   ceil(CTAs / slots) x (ceil(NZ / chunks) + 2r)
 // and minimised over the chunk counts that keep at least max(4, r) planes
 // per chunk: this picks the measured best chunking at every order of the
-// 592^3 workload, and many short chunks on grids that fit in one wave.
-// The TTI kernel and the 16-bit acoustic kernels (more resident CTAs, short
-// fills) run best with more, smaller chunks: about 16 (TTI) or 32 (16-bit
-// acoustic) CTAs per SM in total.
+// 592^3 acoustic workload, ranks the TTI chunkings of the 212^3 grid as
+// measured, and gives many short chunks on grids that fit in one wave.
+// The 16-bit acoustic kernels (more resident CTAs, short fills) run best
+// with more, smaller chunks: about 32 CTAs per SM in total.
 int default_zchunks(const fdw_solver *s) {
   TileGeom tg;
   const bool tti = s->eq == FDW_TTI;
@@ -290,14 +290,15 @@ int default_zchunks(const fdw_solver *s) {
     cudaGetLastError();
     sms = 152;
   }
-  if (tti || s->storage != FDW_F32) {
-    const long per_sm = tti ? 16 : 32;
-    long want = ((long)sms * per_sm + tiles - 1) / tiles;
+  if (!tti && s->storage != FDW_F32) {
+    long want = ((long)sms * 32 + tiles - 1) / tiles;
     if (want > maxch) want = maxch;
     if (want < 1) want = 1;
     return lo > want ? lo : (int)want;
   }
-  int occ = acoustic_ctas_per_sm(s->storage, s->r, s->tile);
+  // FP32 acoustic and TTI: the chunk count that minimises waves x planes
+  // marched per CTA (chunk length + the 2r halo planes)
+  int occ = tti ? tti_ctas_per_sm(s->storage, s->r, s->tile) : acoustic_ctas_per_sm(s->storage, s->r, s->tile);
   if (occ < 1) occ = 1;
   const long slots = (long)sms * occ;
   long best = lo, best_cost = -1;

@@ -131,7 +131,7 @@ struct TTILaunch {
   // level n-1 and of the medium fields
   const CUtensorMap *m_ph, *m_rh, *m_pm, *m_rm, *m_c, *m_e, *m_d, *m_ax, *m_ay;
 };
-constexpr int kTtiTilesMax = 9;  // number of TTI configurations (see tti_kernel.cuh)
+constexpr int kTtiTilesMax = 13;  // number of TTI configurations (see tti_kernel.cuh)
 cudaError_t launch_tti(const TTILaunch &L, cudaStream_t st);
 cudaError_t tti_prepare(int storage, int r, int tile);
 int tti_geom(int storage, int r, int tile, TileGeom *g);

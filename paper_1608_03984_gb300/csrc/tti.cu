@@ -127,12 +127,15 @@ int tti_geom(int storage, int r, int tile, TileGeom *g) {
 }
 
 // Default configuration (measured on the 464^3 TTI workload): four warps
-// per CTA (they beat 2 and 8); up to order 8 the field-pair kernel (z
-// unrolling 4 for FP32, 1 for 16-bit storage), above it the scalar one
-// with z unrolling 2 at orders 10-12 and 1 higher (the queues of 6 fields
-// grow with the order and the pairs' extra registers cost occupancy).
+// per CTA (they beat 2 and 8); up to order 8 the field-pair kernel: at
+// order 6 two rows per thread with z unrolling 2, otherwise one row with z
+// unrolling 4 for FP32 and two rows with z unrolling 1 for 16-bit storage
+// (whose conversions make the shared y taps pay); above order 8 the scalar
+// kernel with z unrolling 2 at orders 10-12 and 1 higher (the queues of 6
+// fields grow with the order and the pairs' extra registers cost occupancy).
 int tti_default_tile(int storage, int r) {
-  if (r <= 4) return storage == FDW_F32 ? 7 : 8;
+  if (r == 3) return 9;
+  if (r <= 4) return storage == FDW_F32 ? 7 : 10;
   return r <= 6 ? 2 : 4;
 }
 

@@ -41,10 +41,10 @@
 
 namespace fdw {
 
-template <typename T, int R, int BY, int NS, int U, bool SH = false>
+template <typename T, int R, int BY, int NS, int U, bool SH = false, int RY = 1>
 struct TtiTile {
   static constexpr int TX = 32;
-  static constexpr int TY = BY;
+  static constexpr int TY = BY * RY;  // RY rows per thread (field-pair kernel)
   static constexpr int EL = (int)sizeof(T);
   static constexpr int XALIGN = 16 / EL;
   static constexpr int HX = ((R + XALIGN - 1) / XALIGN) * XALIGN;
@@ -69,7 +69,7 @@ struct TtiTile {
   static_assert(BXH <= 256 && BYH <= 256, "TMA box dimension limit");
   static_assert((BXH * EL) % 16 == 0 && (TX * EL) % 16 == 0 && (HX * EL) % 16 == 0, "TMA alignment");
   static_assert(SMEM_B <= 227 * 1024, "shared memory per CTA");
-  static_assert(HPW <= 32, "one D_y halo item per lane");
+  static_assert(RY > 1 || HPW <= 32, "one D_y halo item per lane");
   static_assert(2 * R <= 32, "shuffle variant: the row's D_y halo columns fit one warp");
 };
 
@@ -349,8 +349,12 @@ __global__ void __launch_bounds__(32 * BY)
 // on (p, r) pairs with f32x2 instructions (__ffma2_rn, __fadd2_rn,
 // __fmul2_rn; per component the scalar rounding), a difference a - b taken
 // as c1 a + (-c1) b. Fewer issue slots, more registers: faster at orders up
-// to 8, slower above (occupancy).
-template <typename T, int R, int BY, int NS, int U>
+// to 8, slower above (occupancy). With RY > 1 a thread owns RY consecutive
+// rows of its column: the y taps of the rows overlap (2R + RY loads instead
+// of RY (2R + 1)) and the per-plane work (ring wait, barrier, addressing,
+// damping) is shared by RY points; each row's arithmetic is the RY = 1
+// arithmetic, so the results are the same bits.
+template <typename T, int R, int BY, int NS, int U, int RY = 1>
 __global__ void __launch_bounds__(32 * BY)
     tti_tma_pk_kernel(const __grid_constant__ CUtensorMap m_ph, const __grid_constant__ CUtensorMap m_rh,
                       const __grid_constant__ CUtensorMap m_pm, const __grid_constant__ CUtensorMap m_rm,
@@ -358,22 +362,26 @@ __global__ void __launch_bounds__(32 * BY)
                       const __grid_constant__ CUtensorMap m_d, const __grid_constant__ CUtensorMap m_ax,
                       const __grid_constant__ CUtensorMap m_ay, T *__restrict__ p_out,
                       T *__restrict__ r_out, Dims d, Weights w, Sponge sp, int zc, int *err) {
-  using C = TtiTile<T, R, BY, NS, U, false>;
+  using C = TtiTile<T, R, BY, NS, U, false, RY>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-  float *scr = (float *)(smem + NS * C::STAGE_B);  // [2][2][TY][SY] D_y of p and r
+  // [2][TY][SY] (D_y p, D_y r) pairs: one 8-byte load per cross-term tap
+  float2 *scr = (float2 *)(smem + NS * C::STAGE_B);
   uint64_t *bars = (uint64_t *)(smem + NS * C::STAGE_B + C::SCR_B);
   float *gzs = (float *)(smem + NS * C::STAGE_B + C::SCR_B + C::BAR_B);
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + tx;
+  const int ry0 = ty * RY;  // first tile row of this thread
   const int x0 = blockIdx.x * C::TX, y0 = blockIdx.y * C::TY;
   const int z0 = blockIdx.z * zc;
   const int z1 = min(z0 + zc, d.NZ);
   if (z0 >= z1 || zc > kMaxZChunk) return;  // uniform over the CTA
   const int nit = (z1 - z0) + 2 * R;
   const float gxr = (x0 + tx < d.NX) ? sp.gx[x0 + tx] : 0.f;
-  const float gyr = (y0 + ty < d.NY) ? sp.gy[y0 + ty] : 0.f;
+  float gyr[RY];
+#pragma unroll
+  for (int k = 0; k < RY; ++k) gyr[k] = (y0 + ry0 + k < d.NY) ? sp.gy[y0 + ry0 + k] : 0.f;
 
   const CUtensorMap *maps_int[C::N_INT] = {&m_ax, &m_ay, &m_pm, &m_rm, &m_c, &m_e, &m_d, &m_ax, &m_ay};
   if (tid == 0) {
@@ -418,26 +426,32 @@ __global__ void __launch_bounds__(32 * BY)
     for (int j = 0; j < n0; ++j) issue(j);
   }
 
-  // The two fields go through the same stencils with the same weights, so
-  // the arithmetic runs on (p, r) pairs with f32x2 instructions
-  // (__ffma2_rn, __fadd2_rn, __fmul2_rn; per component the scalar
-  // rounding); a difference a - b is taken as c1 a + (-c1) b.
-  // queues of (p, r) pairs: [0] f, [1] D_x f, [2] D_y f
-  float2 q[3][C::QL];
-  float2 dq[C::DL];  // delayed in-plane sums (p_xx + p_yy - A p, A r)
+  // queues of (p, r) pairs per row: [0] f, [1] D_x f, [2] D_y f
+  float2 q[RY][3][C::QL];
+  float2 dq[RY][C::DL];  // delayed in-plane sums (p_xx + p_yy - A p, A r)
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+  for (int k = 0; k < RY; ++k) {
 #pragma unroll
-    for (int i = 0; i < C::QL; ++i) q[a][i] = make_float2(0.f, 0.f);
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-  for (int i = 0; i < C::DL; ++i) dq[i] = make_float2(0.f, 0.f);
+      for (int i = 0; i < C::QL; ++i) q[k][a][i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < C::DL; ++i) dq[k][i] = make_float2(0.f, 0.f);
+  }
 
   const size_t plane = d.plane();
-  const int li = ty * C::TX + tx;  // index inside an interior tile
+  const int li = ry0 * C::TX + tx;  // index of the first row inside an interior tile
   // in-plane second derivatives and axis of the previous head plane, whose
   // cross term is finished one iteration later
-  float2 pfxx = make_float2(0.f, 0.f), pfyy = make_float2(0.f, 0.f);
-  float phx = 0.f, phy = 0.f;
+  float2 pfxx[RY], pfyy[RY];
+  float phx[RY], phy[RY];
+#pragma unroll
+  for (int k = 0; k < RY; ++k) {
+    pfxx[k] = make_float2(0.f, 0.f);
+    pfyy[k] = make_float2(0.f, 0.f);
+    phx[k] = 0.f;
+    phy[k] = 0.f;
+  }
   bool phead = false;
   // A f = nx^2 f_xx + ny^2 f_yy + 2 nx ny f_xy for both fields, and the
   // in-plane sums (f_xx + f_yy - A f for p, A f for r)
@@ -472,75 +486,97 @@ __global__ void __launch_bounds__(32 * BY)
       // its in-plane sums into the delay queue (slot R+u-1; for u = 0 that
       // is the previous group's last slot after the shift)
       if (j >= 1) {
-        float2 a = make_float2(0.f, 0.f);
-        if (phead) {
-          const float *sr0 = scr + (((j - 1) & 1) * 2 * C::TY + ty) * C::SY + R + tx;
-          const float *sr1 = sr0 + C::TY * C::SY;
-          float2 xy = make_float2(0.f, 0.f);
 #pragma unroll
-          for (int m = 1; m <= R; ++m) {
-            xy = __ffma2_rn(w.c1p[m], make_float2(sr0[m], sr1[m]), xy);
-            xy = __ffma2_rn(w.c1n[m], make_float2(sr0[-m], sr1[-m]), xy);
+        for (int k = 0; k < RY; ++k) {
+          float2 a = make_float2(0.f, 0.f);
+          if (phead) {
+            const float2 *sr = scr + (((j - 1) & 1) * C::TY + ry0 + k) * C::SY + R + tx;
+            float2 xy = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int m = 1; m <= R; ++m) {
+              xy = __ffma2_rn(w.c1p[m], sr[m], xy);
+              xy = __ffma2_rn(w.c1n[m], sr[-m], xy);
+            }
+            a = inplane(phx[k], phy[k], pfxx[k], pfyy[k], xy);
           }
-          a = inplane(phx, phy, pfxx, pfyy, xy);
+          dq[k][R + u - 1] = a;
         }
-        dq[R + u - 1] = a;
       }
 
       const unsigned char *st = smem + s * C::STAGE_B;
       const int zh = z0 - R + j;
       const bool head = (zh >= 0 && zh < d.NZ);
-      float *sb = scr + (j & 1) * 2 * C::TY * C::SY;
+      float2 *sb = scr + (j & 1) * C::TY * C::SY;
       if (head) {
         const T *Hp = (const T *)st;
         const T *Hr = (const T *)(st + C::HALO_B);
-        const int o0 = (ty + R) * C::BXH + C::HX + tx;
+        const int o0 = (ry0 + R) * C::BXH + C::HX + tx;
         auto pr = [&](int o) { return make_float2(St<T>::ld(Hp[o]), St<T>::ld(Hr[o])); };
-        const float2 fc = pr(o0);
-        float2 xx = __fmul2_rn(w.w2p[0], fc), yy = xx, dx = make_float2(0.f, 0.f), dy = dx;
+        // with RY > 1 the column at x over rows ry0 - R .. ry0 + RY - 1 + R
+        // is loaded once for the RY rows' y taps
+        float2 cv[RY > 1 ? 2 * R + RY : 1];
+        if constexpr (RY > 1) {
 #pragma unroll
-        for (int m = 1; m <= R; ++m) {
-          const float2 xp = pr(o0 + m), xm = pr(o0 - m);
-          const float2 yp = pr(o0 + m * C::BXH), ym = pr(o0 - m * C::BXH);
-          xx = __ffma2_rn(w.w2p[m], __fadd2_rn(xp, xm), xx);
-          dx = __ffma2_rn(w.c1n[m], xm, __ffma2_rn(w.c1p[m], xp, dx));
-          yy = __ffma2_rn(w.w2p[m], __fadd2_rn(yp, ym), yy);
-          dy = __ffma2_rn(w.c1n[m], ym, __ffma2_rn(w.c1p[m], yp, dy));
+          for (int i = 0; i < 2 * R + RY; ++i) cv[i] = pr(o0 + (i - R) * C::BXH);
         }
-        pfxx = xx;
-        pfyy = yy;
-        q[0][2 * R + u] = fc;
-        q[1][2 * R + u] = dx;
-        q[2][2 * R + u] = dy;
-        {
-          sb[ty * C::SY + R + tx] = dy.x;
-          sb[(C::TY + ty) * C::SY + R + tx] = dy.y;
-          // D_y of both fields in the x halo columns [-R, 0) and
-          // [32, 32 + R): HPW items per warp, one per lane
-          if (tx < C::HPW) {
-            const int t = ty * C::HPW + tx;
-            if (t < C::NHALO) {
-              const int f = t / (2 * R * C::TY);
-              const int rem = t - f * (2 * R * C::TY);
-              const int yy_ = rem / (2 * R);
-              const int k = rem - yy_ * (2 * R);
-              const int xo = k < R ? k - R : C::TX + (k - R);  // tile x of the halo column
-              const T *H = (const T *)(st + f * C::HALO_B);
-              const T *col = H + (yy_ + R) * C::BXH + C::HX + xo;
-              float dyh = 0.f;
+        auto col = [&](int k, int i) {  // row k + i of the column
+          if constexpr (RY > 1)
+            return cv[R + k + i];
+          else
+            return pr(o0 + i * C::BXH);
+        };
 #pragma unroll
-              for (int m = 1; m <= R; ++m)
-                dyh = fmaf(w.c1[m], St<T>::ld(col[m * C::BXH]) - St<T>::ld(col[-m * C::BXH]), dyh);
-              sb[(f * C::TY + yy_) * C::SY + R + xo] = dyh;
-            }
+        for (int k = 0; k < RY; ++k) {
+          const int ob = o0 + k * C::BXH;
+          const float2 fc = col(k, 0);
+          float2 xx = __fmul2_rn(w.w2p[0], fc), yy = xx, dx = make_float2(0.f, 0.f), dy = dx;
+#pragma unroll
+          for (int m = 1; m <= R; ++m) {
+            const float2 xp = pr(ob + m), xm = pr(ob - m);
+            const float2 yp = col(k, m), ym = col(k, -m);
+            xx = __ffma2_rn(w.w2p[m], __fadd2_rn(xp, xm), xx);
+            dx = __ffma2_rn(w.c1n[m], xm, __ffma2_rn(w.c1p[m], xp, dx));
+            yy = __ffma2_rn(w.w2p[m], __fadd2_rn(yp, ym), yy);
+            dy = __ffma2_rn(w.c1n[m], ym, __ffma2_rn(w.c1p[m], yp, dy));
           }
-          const T *HA = (const T *)(st + 2 * C::HALO_B);
-          phx = St<T>::ld(HA[li]);
-          phy = St<T>::ld(HA[C::INT_B / C::EL + li]);
+          pfxx[k] = xx;
+          pfyy[k] = yy;
+          q[k][0][2 * R + u] = fc;
+          q[k][1][2 * R + u] = dx;
+          q[k][2][2 * R + u] = dy;
+          sb[(ry0 + k) * C::SY + R + tx] = dy;
+        }
+        // D_y of both fields in the x halo columns [-R, 0) and
+        // [32, 32 + R): HPW items per warp, spread over its lanes
+#pragma unroll
+        for (int i = 0; i < C::HPW; i += 32) {
+          const int t = ty * C::HPW + i + tx;
+          if (i + tx < C::HPW && t < C::NHALO) {
+            const int f = t / (2 * R * C::TY);
+            const int rem = t - f * (2 * R * C::TY);
+            const int yy_ = rem / (2 * R);
+            const int k = rem - yy_ * (2 * R);
+            const int xo = k < R ? k - R : C::TX + (k - R);  // tile x of the halo column
+            const T *H = (const T *)(st + f * C::HALO_B);
+            const T *hc = H + (yy_ + R) * C::BXH + C::HX + xo;
+            float dyh = 0.f;
+#pragma unroll
+            for (int m = 1; m <= R; ++m)
+              dyh = fmaf(w.c1[m], St<T>::ld(hc[m * C::BXH]) - St<T>::ld(hc[-m * C::BXH]), dyh);
+            reinterpret_cast<float *>(sb + yy_ * C::SY + R + xo)[f] = dyh;
+          }
+        }
+        const T *HA = (const T *)(st + 2 * C::HALO_B);
+#pragma unroll
+        for (int k = 0; k < RY; ++k) {
+          phx[k] = St<T>::ld(HA[li + k * C::TX]);
+          phy[k] = St<T>::ld(HA[C::INT_B / C::EL + li + k * C::TX]);
         }
       } else {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) q[a][2 * R + u] = make_float2(0.f, 0.f);
+        for (int k = 0; k < RY; ++k)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) q[k][a][2 * R + u] = make_float2(0.f, 0.f);
       }
       phead = head;
       if (j < 2 * R) continue;
@@ -548,36 +584,45 @@ __global__ void __launch_bounds__(32 * BY)
       // output plane zo = zh - R
       const int zo = zh - R;
       const T *O = (const T *)(st + 2 * C::HALO_B);
-      auto tileval = [&](int i) { return St<T>::ld(O[i * (C::INT_B / C::EL) + li]); };
-      const float pm = tileval(2), rm = tileval(3), cc = tileval(4), ee = tileval(5), dd = tileval(6);
-      const float nx = tileval(7), ny = tileval(8);
-      const float nz = sqrtf(fmaxf(0.f, 1.f - nx * nx - ny * ny));
-      float2 zz = __fmul2_rn(w.w2p[0], q[0][u + R]), xz = make_float2(0.f, 0.f), yz = xz;
+      const float gzo = gzs[zo - z0];
 #pragma unroll
-      for (int m = 1; m <= R; ++m) {
-        zz = __ffma2_rn(w.w2p[m], __fadd2_rn(q[0][u + R + m], q[0][u + R - m]), zz);
-        xz = __ffma2_rn(w.c1n[m], q[1][u + R - m], __ffma2_rn(w.c1p[m], q[1][u + R + m], xz));
-        yz = __ffma2_rn(w.c1n[m], q[2][u + R - m], __ffma2_rn(w.c1p[m], q[2][u + R + m], yz));
-      }
-      const float Hp = dq[u].x + (1.f - nz * nz) * zz.x - 2.f * nz * (nx * xz.x + ny * yz.x);
-      const float Gr = dq[u].y + nz * nz * zz.y + 2.f * nz * (nx * xz.y + ny * yz.y);
-      const float gh = gxr + gyr + gzs[zo - z0];
-      const float inv = __fdividef(1.f, 1.f + gh), qq = 1.f - gh;
-      const float pn = (2.f * q[0][u + R].x - qq * pm + cc * (ee * Hp + dd * Gr)) * inv;
-      const float rn = (2.f * q[0][u + R].y - qq * rm + cc * (dd * Hp + Gr)) * inv;
-      const int x = x0 + tx, y = y0 + ty;
-      if (x < d.NX && y < d.NY) {
-        const size_t o = (size_t)zo * plane + (size_t)y * d.Xp + x;
-        p_out[o] = St<T>::st(pn);
-        r_out[o] = St<T>::st(rn);
+      for (int k = 0; k < RY; ++k) {
+        const int lk = li + k * C::TX;
+        auto tileval = [&](int i) { return St<T>::ld(O[i * (C::INT_B / C::EL) + lk]); };
+        const float pm = tileval(2), rm = tileval(3), cc = tileval(4), ee = tileval(5), dd = tileval(6);
+        const float nx = tileval(7), ny = tileval(8);
+        const float nz = sqrtf(fmaxf(0.f, 1.f - nx * nx - ny * ny));
+        const float2 *f0 = q[k][0], *f1 = q[k][1], *f2 = q[k][2];
+        float2 zz = __fmul2_rn(w.w2p[0], f0[u + R]), xz = make_float2(0.f, 0.f), yz = xz;
+#pragma unroll
+        for (int m = 1; m <= R; ++m) {
+          zz = __ffma2_rn(w.w2p[m], __fadd2_rn(f0[u + R + m], f0[u + R - m]), zz);
+          xz = __ffma2_rn(w.c1n[m], f1[u + R - m], __ffma2_rn(w.c1p[m], f1[u + R + m], xz));
+          yz = __ffma2_rn(w.c1n[m], f2[u + R - m], __ffma2_rn(w.c1p[m], f2[u + R + m], yz));
+        }
+        const float Hp = dq[k][u].x + (1.f - nz * nz) * zz.x - 2.f * nz * (nx * xz.x + ny * yz.x);
+        const float Gr = dq[k][u].y + nz * nz * zz.y + 2.f * nz * (nx * xz.y + ny * yz.y);
+        const float gh = gxr + gyr[k] + gzo;
+        const float inv = __fdividef(1.f, 1.f + gh), qq = 1.f - gh;
+        const float pn = (2.f * f0[u + R].x - qq * pm + cc * (ee * Hp + dd * Gr)) * inv;
+        const float rn = (2.f * f0[u + R].y - qq * rm + cc * (dd * Hp + Gr)) * inv;
+        const int x = x0 + tx, y = y0 + ry0 + k;
+        if (x < d.NX && y < d.NY) {
+          const size_t o = (size_t)zo * plane + (size_t)y * d.Xp + x;
+          p_out[o] = St<T>::st(pn);
+          r_out[o] = St<T>::st(rn);
+        }
       }
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < RY; ++k) {
 #pragma unroll
-      for (int i = 0; i < 2 * R; ++i) q[a][i] = q[a][i + U];
+      for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int i = 0; i < R; ++i) dq[i] = dq[i + U];
+        for (int i = 0; i < 2 * R; ++i) q[k][a][i] = q[k][a][i + U];
+#pragma unroll
+      for (int i = 0; i < R; ++i) dq[k][i] = dq[k][i + U];
+    }
   }
 }
 
@@ -587,12 +632,14 @@ namespace fdw {
 
 constexpr int kTtiNS = 4;
 
-// Candidate configurations (warps per CTA = tile rows BY, z unrolling U,
-// variant: 0 scalar with the cross term through the shared D_y scratch,
-// 1 scalar with warp shuffles, 2 field pairs with the scratch), selected at
-// run time by index. The shuffle form needs four shuffles per
-// tap (interior and halo lane, both sides) where the scratch needs two
-// shared loads, and measures 17-25% slower; it stays selectable.
+// Candidate configurations (warps per CTA BY, z unrolling U, variant: 0
+// scalar with the cross term through the shared D_y scratch, 1 scalar with
+// warp shuffles, 2 field pairs with the scratch, 3 field pairs with two rows
+// per thread), selected at run time by index. The shuffle form needs four
+// shuffles per tap (interior and halo lane, both sides) where the scratch
+// needs two shared loads, and measures 17-25% slower; it stays selectable.
+// Variant 3 exists up to order 8 (radius 4): above it the two rows' z
+// queues do not fit the registers.
 #define FDW_TTI_CFGS(X) \
   X(0, 8, 2, 0)         \
   X(1, 4, 4, 0)         \
@@ -602,15 +649,24 @@ constexpr int kTtiNS = 4;
   X(5, 4, 4, 1)         \
   X(6, 4, 2, 1)         \
   X(7, 4, 4, 2)         \
-  X(8, 4, 1, 2)
-constexpr int kTtiTiles = 9;
+  X(8, 4, 1, 2)         \
+  X(9, 4, 2, 3)         \
+  X(10, 4, 1, 3)        \
+  X(11, 2, 2, 3)        \
+  X(12, 4, 4, 3)
+constexpr int kTtiTiles = 13;
+constexpr int kTtiRowPairMaxR = 4;
+
+constexpr int tti_rows_per_thread(int V) { return V == 3 ? 2 : 1; }
+template <int R, int V>
+constexpr bool tti_cfg_exists() { return tti_rows_per_thread(V) == 1 || R <= kTtiRowPairMaxR; }
 
 template <typename T, int R, int BY, int U, int V>
-cudaError_t launch_tti_cfg(const TTILaunch &L, cudaStream_t st) {
-  using C = TtiTile<T, R, BY, kTtiNS, U, V == 1>;
+cudaError_t launch_tti_cfg_impl(const TTILaunch &L, cudaStream_t st) {
+  using C = TtiTile<T, R, BY, kTtiNS, U, V == 1, tti_rows_per_thread(V)>;
   auto kern = [] {
-    if constexpr (V == 2)
-      return tti_tma_pk_kernel<T, R, BY, kTtiNS, U>;
+    if constexpr (V >= 2)
+      return tti_tma_pk_kernel<T, R, BY, kTtiNS, U, tti_rows_per_thread(V)>;
     else
       return tti_tma_kernel<T, R, BY, kTtiNS, U, V == 1>;
   }();
@@ -632,19 +688,32 @@ cudaError_t launch_tti_cfg(const TTILaunch &L, cudaStream_t st) {
 }
 
 template <typename T, int R, int BY, int U, int V>
-void tti_geom_cfg(TileGeom *g) {
-  using C = TtiTile<T, R, BY, kTtiNS, U, V == 1>;
-  g->box_halo_x = C::BXH;
-  g->box_halo_y = C::BYH;
-  g->box_int_x = C::TX;
-  g->box_int_y = C::TY;
-  g->smem = C::SMEM_B;
+cudaError_t launch_tti_cfg(const TTILaunch &L, cudaStream_t st) {
+  if constexpr (tti_cfg_exists<R, V>())
+    return launch_tti_cfg_impl<T, R, BY, U, V>(L, st);
+  else
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int R, int BY, int U, int V>
+int tti_geom_cfg(TileGeom *g) {
+  if constexpr (!tti_cfg_exists<R, V>()) {
+    return -1;
+  } else {
+    using C = TtiTile<T, R, BY, kTtiNS, U, V == 1, tti_rows_per_thread(V)>;
+    g->box_halo_x = C::BXH;
+    g->box_halo_y = C::BYH;
+    g->box_int_x = C::TX;
+    g->box_int_y = C::TY;
+    g->smem = C::SMEM_B;
+    return 0;
+  }
 }
 
 #define FDW_TTI_CASE_LAUNCH(ID, BY, U, V) \
   case ID: return launch_tti_cfg<TYPE_, R, BY, U, V>(L, st);
 #define FDW_TTI_CASE_GEOM(ID, BY, U, V) \
-  case ID: tti_geom_cfg<TYPE_, R, BY, U, V>(g); return 0;
+  case ID: return tti_geom_cfg<TYPE_, R, BY, U, V>(g);
 
 #define FDW_TTI_DEFINE_STORAGE(SUFFIX, TYPE)                                  \
   template <typename TYPE_, int R>                                            \

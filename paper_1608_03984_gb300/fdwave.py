@@ -435,7 +435,8 @@ class Solver:
         _chk(lib().fdw_set_zchunks(self._h, int(zchunks)))
 
     def set_tile_config(self, tile):
-        """Tile configuration of the 2.5D kernel (acoustic 0..12, TTI 0..8), -1 = default."""
+        """Tile configuration of the 2.5D kernel (acoustic 0..12, TTI 0..12 with
+        9..12 up to order 8), -1 = default."""
         _chk(lib().fdw_set_tile_config(self._h, int(tile)))
 
     @property

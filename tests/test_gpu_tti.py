@@ -127,14 +127,24 @@ def test_vti_matches_oracle(fdw, O):
     s.close()
 
 
+ROW_PAIR_TILES = (9, 10, 11, 12)  # two rows per thread, orders up to 8
+NTILES = 13
+
+
 @pytest.mark.parametrize("order", [2, 8, 12, 16])
-@pytest.mark.parametrize("tile", list(range(9)))
+@pytest.mark.parametrize("tile", list(range(NTILES)))
 def test_every_tti_configuration(fdw, O, order, tile):
-    """Each (warps per CTA, z unrolling) configuration of the TTI kernel
-    reproduces the oracle's step (ragged tile tails in x, y and z), and
-    a few more steps stay finite."""
+    """Each (warps per CTA, z unrolling, variant) configuration of the TTI
+    kernel reproduces the oracle's step (ragged tile tails in x, y and z),
+    and a few more steps stay finite. The two-rows-per-thread
+    configurations exist up to order 8 and are refused above."""
     w = small_tti(n=(23, 13, 37), order=order, seed=70 + order)
     s = tti_solver(fdw, w)
+    if tile in ROW_PAIR_TILES and order > 8:
+        with pytest.raises(fdw.FdwError):
+            s.set_tile_config(tile)
+        s.close()
+        return
     s.set_tile_config(tile)
     assert s.tile_config == tile
     comp = s.comp_shape
@@ -150,6 +160,29 @@ def test_every_tti_configuration(fdw, O, order, tile):
     s.step(3)
     s.check()
     s.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("order", [2, 4, 8])
+def test_row_pair_kernel_same_bits(fdw, order, storage):
+    """Two rows per thread changes which thread computes a point, not its
+    arithmetic: the row-pair configurations give the same bits as the
+    one-row field-pair kernel with the same z unrolling (ragged tails in x,
+    y and z, several steps with a source)."""
+    w = small_tti(n=(29, 19, 41), order=order, nt=6, seed=90 + order)
+    out = {}
+    same = ((7, 12), (8, 10))
+    for tile in sorted({t for p in same for t in p}):
+        s = tti_solver(fdw, w, storage=storage)
+        s.set_tile_config(tile)
+        s.step(w.nt)
+        out[tile] = (s.wavefield(0, 0), s.wavefield(1, 0), s.traces())
+        s.check()
+        s.close()
+    for a, b in same:
+        for x, y in zip(out[a], out[b]):
+            assert np.array_equal(x, y), (a, b)
+    assert np.abs(out[7][0]).max() > 0
 
 
 @pytest.mark.parametrize("order", [8, 12])
