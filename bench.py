@@ -87,6 +87,14 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def launches_per_step(nrec):
+    """Kernels of one forward step: the stencil, then the source injection
+    and the receiver interpolation -- one block for both up to 256
+    receivers (or the injection alone without receivers), two kernels
+    above."""
+    return 3 if nrec > 256 else 2
+
+
 def kernel_source_sha(root=ROOT):
     """Hash of the acoustic stencil kernel's source (template + dispatch + PTX
     helpers), comments and white space removed: any change of the code
@@ -427,7 +435,8 @@ def run_fdwave(args, orders):
             "data": "synthetic", "config": config_dict(args, orders, base),
             "roofline": roof, "per_order": per_order, "e2e": e2e, "cpu_baseline": cpu, "tti": tti,
             "fwi": fwi_res, "storage": storage, "closure": closure_res, "config1": cfg1,
-            "paper_model_gb300": paper, "clocks": clk, "gpu_launches": 3 * len(orders) * args.steps,
+            "paper_model_gb300": paper, "clocks": clk,
+            "gpu_launches": launches_per_step(base.rec_xyz.shape[0]) * len(orders) * args.steps,
         }
         line = headline(full, args.details)
         try:

@@ -111,9 +111,59 @@ __global__ void __launch_bounds__(256) adjoint_spread_kernel(SparseLaunch L) {
   atomic_add_st<T>((T *)L.f0 + p, cc * L.res_scale * wt * (res * L.amp_scale) * __frcp_rn(1.f + gh));
 }
 
+// Forward step with at most kFusedRec receivers: injection and receiver
+// interpolation in one block (one launch instead of two; the block barrier
+// orders the injection's atomics before the receivers' reads). Same
+// arithmetic as inject_kernel + gather_kernel.
+constexpr int kFusedRec = 256;  // one receiver per thread of the block
+
+template <typename T>
+__global__ void __launch_bounds__(256) inject_gather_kernel(SparseLaunch L) {
+  __shared__ int sn;
+  if (threadIdx.x == 0) sn = *L.step;
+  __syncthreads();
+  const int n = sn;
+  if (threadIdx.x == 0) *L.step = n + 1;
+  const size_t plane = L.d.plane();
+  if (n >= 0 && n < L.nt_src) {
+    for (int t = threadIdx.x; t < L.nsrc * 8; t += blockDim.x) {
+      const float wt = L.src_w[t];
+      if (wt == 0.f) continue;
+      const int s = t >> 3;
+      const int i = L.src_corner[t * 3 + 0], j = L.src_corner[t * 3 + 1], k = L.src_corner[t * 3 + 2];
+      const size_t p = (size_t)k * plane + (size_t)j * L.d.Xp + i;
+      const float amp = L.wavelet[(size_t)n * L.nsrc + s];
+      const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[k];
+      const float cc = St<T>::ld(((const T *)L.c)[p]);
+      const float v = cc * wt * (amp * L.amp_scale) * __frcp_rn(1.f + gh);
+      atomic_add_st<T>((T *)L.f0 + p, v);
+      if (L.f1) atomic_add_st<T>((T *)L.f1 + p, v);
+    }
+  }
+  __syncthreads();
+  const int n1 = n + 1;  // level just produced
+  const int r = threadIdx.x;
+  if (r >= L.nrec || n1 < 0 || n1 > L.nt_rec) return;
+  const T *f = (const T *)L.f0;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int t = r * 8 + q;
+    const float wt = L.rec_w[t];
+    const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], k = L.rec_corner[t * 3 + 2];
+    const float v = St<T>::ld(f[(size_t)k * plane + (size_t)j * L.d.Xp + i]);
+    acc += (double)wt * (double)v;
+  }
+  L.traces[(size_t)n1 * L.nrec + r] = acc * L.trace_scale;
+}
+
 template <typename T>
 static cudaError_t launch_sparse_t(const SparseLaunch &L, cudaStream_t st) {
   cudaError_t e;
+  if (!L.adjoint && L.nrec > 0 && L.nrec <= kFusedRec && L.traces) {
+    inject_gather_kernel<T><<<1, 256, 0, st>>>(L);
+    return cudaGetLastError();
+  }
   if (L.adjoint && L.residual && L.nrec > 0) {
     adjoint_spread_kernel<T><<<(L.nrec * 8 + 255) / 256, 256, 0, st>>>(L);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -134,3 +134,13 @@ def test_headline_line_is_compact_and_complete():
     for k in ("tti", "storage", "fwi", "closure", "config1"):
         full[k] = None
     assert bench.headline(full, "d.json")["sections"] == {}
+
+
+def test_launches_per_step_follows_the_sparse_kernels():
+    """One fused injection + interpolation block up to 256 receivers, two
+    kernels above (the stencil is the third)."""
+    assert bench.launches_per_step(0) == 2
+    assert bench.launches_per_step(32) == 2
+    assert bench.launches_per_step(256) == 2
+    assert bench.launches_per_step(257) == 3
+    assert bench.launches_per_step(65536) == 3
