@@ -530,6 +530,14 @@ extern "C" int fdw_create(fdw_solver **out, int nx, int ny, int nz, double h, in
   if (equation == FDW_TTI) {
     try_alloc(&s->e, fb); try_alloc(&s->dl, fb); try_alloc(&s->ax, fb); try_alloc(&s->ay, fb);
   }
+  // the physical model's copies, filled by fdw_set_model (allocated here so
+  // that setting a model allocates nothing)
+  const size_t nphys = (size_t)nx * ny * nz * sizeof(float);
+  try_alloc((void **)&s->vp, nphys);
+  if (equation == FDW_TTI) {
+    try_alloc((void **)&s->eps, nphys); try_alloc((void **)&s->delta, nphys);
+    try_alloc((void **)&s->theta, nphys); try_alloc((void **)&s->phi, nphys);
+  }
   try_alloc((void **)&s->gam[0], sizeof(float) * NX);
   try_alloc((void **)&s->gam[1], sizeof(float) * NY);
   try_alloc((void **)&s->gam[2], sizeof(float) * NZ);
