@@ -10,7 +10,8 @@
 // in factored form (first derivative of a first derivative): the same
 // discrete operator with O(k) instead of O(k^2) operations per point.
 //
-// Geometry. A CTA owns a 32 x TY column (one point per thread) and marches a
+// Geometry. A CTA owns a 32 x TY column (one point per thread; the field-pair
+// kernel can also take RY = 2 consecutive rows per thread) and marches a
 // chunk of z planes. Everything that needs x/y neighbours is computed when a
 // plane enters the march as the HEAD plane z+r, from one TMA halo tile per
 // field:
