@@ -30,7 +30,7 @@ constexpr int kOffW1 = 0, kOffB1 = kH * 3 * 27, kOffW2 = kOffB1 + kH, kOffB2 = k
               kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * 27, kNumParams = kOffB3 + 1;
 constexpr float kVelMean = 3000.f, kVelScale = 750.f;
 constexpr int kBwdChunks = 16;  // partial sums per weight-gradient pair
-constexpr int kHalo = 3;        // receptive-field radius of the three 3x3x3 layers
+constexpr int kHalo = kClosureHalo;  // receptive-field radius of the three 3x3x3 layers
 
 // ---------------------------------------------------------------------------
 // convolutions

@@ -207,12 +207,12 @@ __global__ void tc_inputs_kernel(const T *__restrict__ u, const T *__restrict__ 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(tc::NTHR, 1)
     closure_tc_kernel(const uint2 *__restrict__ x16, const TcWeights *__restrict__ wg, float *__restrict__ out,
-                      int NX, int NY, int NZ, int zc) {
+                      int NX, int NY, int NZ, int ox, int oy, int oz, int zend, int zc) {
   using namespace tc;
   extern __shared__ __align__(16) unsigned char sm[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, NZ);
+  const int X0 = ox + blockIdx.x * TX, Y0 = oy + blockIdx.y * TY;
+  const int z0 = oz + blockIdx.z * zc, z1 = min(z0 + zc, zend);
   if (z0 >= z1) return;
 
   // weights and biases into shared memory; each 16 x 16 matrix's rows are
@@ -490,24 +490,34 @@ int closure_tc_reserve(ClosureNet *c, Dims d) {
   return 0;
 }
 
-// net(x) on the grid into `dst` (FP32 dense [NZ][NY][NX]); u == null: x0.
-// Variant 0 runs the tcgen05 kernel, variant 2 the mma.sync kernel.
+// net(x) into `dst` (FP32 dense [NZ][NY][NX]) on the output box, the
+// points the correction is applied to; u == null: x0. Variant 0 runs the
+// tcgen05 kernel, variant 2 the mma.sync kernel.
 template <typename T>
 static cudaError_t tc_net(ClosureNet *c, const T *u, const T *um, const float *vp, int nx, int ny, int nz, int nb,
                           Dims d, float *dst, int *err, cudaStream_t st) {
   const long rows = (long)d.NY * d.NZ;
   tc_inputs_kernel<T><<<(int)(rows < 152 * 64 ? rows : 152 * 64), 256, 0, st>>>(u, um, vp, nx, ny, nz, nb, d,
                                                                                 c->s_dev, (uint2 *)c->x16);
-  if (c->variant == 0) return closure_umma_run(c, c->x16, dst, d, err, st);
-  const int tiles = ((d.NX + tc::TX - 1) / tc::TX) * ((d.NY + tc::TY - 1) / tc::TY);
+  const int n[3] = {nx, ny, nz};
+  NetBox box;
+  for (int a = 0; a < 3; ++a) {
+    box.lo[a] = nb + kClosureHalo;
+    box.hi[a] = nb + n[a] - kClosureHalo;
+  }
+  if (c->variant == 0) return closure_umma_run(c, c->x16, dst, d, box, err, st);
+  if (box.empty()) return cudaGetLastError();
+  const int bx = box.hi[0] - box.lo[0], by = box.hi[1] - box.lo[1], bz = box.hi[2] - box.lo[2];
+  const int tiles = ((bx + tc::TX - 1) / tc::TX) * ((by + tc::TY - 1) / tc::TY);
   int zch = (2 * 152 + tiles - 1) / tiles;  // about two CTAs per SM in total
   if (zch < 1) zch = 1;
-  const int zmax = d.NZ / 16 > 0 ? d.NZ / 16 : 1;  // chunks of >= 16 planes (the z halo is 5 planes)
+  const int zmax = bz / 16 > 0 ? bz / 16 : 1;  // chunks of >= 16 planes (the z halo is 5 planes)
   if (zch > zmax) zch = zmax;
-  const int zc = (d.NZ + zch - 1) / zch;
-  dim3 grd((d.NX + tc::TX - 1) / tc::TX, (d.NY + tc::TY - 1) / tc::TY, (d.NZ + zc - 1) / zc);
+  const int zc = (bz + zch - 1) / zch;
+  dim3 grd((bx + tc::TX - 1) / tc::TX, (by + tc::TY - 1) / tc::TY, (bz + zc - 1) / zc);
   closure_tc_kernel<<<grd, tc::NTHR, tc::SMEM_B, st>>>((const uint2 *)c->x16, (const TcWeights *)c->tcw, dst,
-                                                       d.NX, d.NY, d.NZ, zc);
+                                                       d.NX, d.NY, d.NZ, box.lo[0], box.lo[1], box.lo[2],
+                                                       box.hi[2], zc);
   return cudaGetLastError();
 }
 

@@ -264,7 +264,8 @@ __global__ void umma_prepare_kernel(const __nv_bfloat16 *__restrict__ pb, const 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(um::NTHR, 1)
     closure_umma_kernel(const uint2 *__restrict__ x16, const UmmaWeights *__restrict__ wg, float *__restrict__ out,
-                        int NX, int NY, int NZ, int tiles_x, int tiles_y, int zc, int nitems, int *err) {
+                        int NX, int NY, int NZ, int ox, int oy, int oz, int zend, int tiles_x, int tiles_y,
+                        int zc, int nitems, int *err) {
   using namespace um;
   using namespace umx;
   extern __shared__ unsigned char smem_raw[];
@@ -362,9 +363,9 @@ __global__ void __launch_bounds__(um::NTHR, 1)
     };
     for (int item = blockIdx.x; item < nitems && !*abort_flag; item += gridDim.x) {
       const int tt = item % tiles, zk = item / tiles;
-      X0 = (tt % tiles_x) * TXO;
-      Y0 = (tt / tiles_x) * TYO;
-      const int z0 = zk * zc, z1 = min(z0 + zc, NZ), nit = z1 - z0 + 6;
+      X0 = ox + (tt % tiles_x) * TXO;
+      Y0 = oy + (tt / tiles_x) * TYO;
+      const int z0 = oz + zk * zc, z1 = min(z0 + zc, zend), nit = z1 - z0 + 6;
       fetch(z0 - 3);
       for (int s = 0; s < nit; ++s) {
         const int b = fills & 1;
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(um::NTHR, 1)
       };
       for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
         const int zk = item / tiles;
-        const int z0 = zk * zc, z1 = min(z0 + zc, NZ), nit = z1 - z0 + 6;
+        const int z0 = oz + zk * zc, z1 = min(z0 + zc, zend), nit = z1 - z0 + 6;
         // tensor memory cleared for the item (layer-1 and layer-2 slots)
         ok = uwait(BAR_Z1, gz & 1) && uwait(BAR_Z2, gz & 1) && L1(z0 - 3);
         ++gz;
@@ -485,8 +486,8 @@ __global__ void __launch_bounds__(um::NTHR, 1)
     for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
       const int tt = item % tiles, zk = item / tiles;
-      const int X0 = (tt % tiles_x) * TXO, Y0 = (tt / tiles_x) * TYO;
-      const int z0 = zk * zc, z1 = min(z0 + zc, NZ), nit = z1 - z0 + 6;
+      const int X0 = ox + (tt % tiles_x) * TXO, Y0 = oy + (tt / tiles_x) * TYO;
+      const int z0 = oz + zk * zc, z1 = min(z0 + zc, zend), nit = z1 - z0 + 6;
       for (uint32_t col = 0; col < 192; col += 16) st16_zero(tmem + lanes + tm0 + col);
       wait_st();
       fence_before();
@@ -582,8 +583,8 @@ __global__ void __launch_bounds__(um::NTHR, 1)
     }
     for (int item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
       const int tt = item % tiles, zk = item / tiles;
-      const int X0 = (tt % tiles_x) * TXO, Y0 = (tt / tiles_x) * TYO;
-      const int z0 = zk * zc, z1 = min(z0 + zc, NZ), nit = z1 - z0 + 6;
+      const int X0 = ox + (tt % tiles_x) * TXO, Y0 = oy + (tt / tiles_x) * TYO;
+      const int z0 = oz + zk * zc, z1 = min(z0 + zc, zend), nit = z1 - z0 + 6;
       for (int s = 0; s < nit; ++s) {
         const bool ok = wait(BAR_L3, gl3 & 1);
         // one decision for the warpgroup; also the point where the previous
@@ -656,36 +657,41 @@ cudaError_t closure_umma_prepare(ClosureNet *c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Work items: output columns of TXO x TYO points times z chunks; the chunk
-// count minimises the slowest CTA's plane iterations, ceil(items / CTAs) x
-// (chunk + 6), the 6 being the z halo of the three layers.
-cudaError_t closure_umma_run(ClosureNet *c, const void *x16, float *dst, Dims d, int *err, cudaStream_t st) {
+// Work items: output columns of TXO x TYO points times z chunks covering
+// the output box; the chunk count minimises the slowest CTA's plane
+// iterations, ceil(items / CTAs) x (chunk + 6), the 6 being the z halo of
+// the three layers.
+cudaError_t closure_umma_run(ClosureNet *c, const void *x16, float *dst, Dims d, const NetBox &box, int *err,
+                             cudaStream_t st) {
+  if (box.empty()) return cudaSuccess;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                  cudaSuccess || sms < 1) {
     cudaGetLastError();
     sms = 152;
   }
-  const int tiles_x = (d.NX + um::TXO - 1) / um::TXO, tiles_y = (d.NY + um::TYO - 1) / um::TYO;
+  const int bx = box.hi[0] - box.lo[0], by = box.hi[1] - box.lo[1], bz = box.hi[2] - box.lo[2];
+  const int tiles_x = (bx + um::TXO - 1) / um::TXO, tiles_y = (by + um::TYO - 1) / um::TYO;
   const long tiles = (long)tiles_x * tiles_y;
   int best_ch = 1;
   long best_cost = -1;
-  const int max_ch = d.NZ / 8 > 1 ? d.NZ / 8 : 1;
+  const int max_ch = bz / 8 > 1 ? bz / 8 : 1;
   for (int ch = 1; ch <= max_ch; ++ch) {
-    const int zc = (d.NZ + ch - 1) / ch;
-    const long items = tiles * ((d.NZ + zc - 1) / zc);
+    const int zc = (bz + ch - 1) / ch;
+    const long items = tiles * ((bz + zc - 1) / zc);
     const long cost = ((items + sms - 1) / sms) * (zc + 6);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
       best_ch = ch;
     }
   }
-  const int zc = (d.NZ + best_ch - 1) / best_ch;
-  const long nitems = tiles * ((d.NZ + zc - 1) / zc);
+  const int zc = (bz + best_ch - 1) / best_ch;
+  const long nitems = tiles * ((bz + zc - 1) / zc);
   if (nitems > 0x7fffffffL) return cudaErrorInvalidValue;
   const int grid = (int)(nitems < sms ? nitems : sms);
   closure_umma_kernel<<<grid, um::NTHR, um::SMEM_B, st>>>((const uint2 *)x16, (const UmmaWeights *)c->umw, dst,
-                                                           d.NX, d.NY, d.NZ, tiles_x, tiles_y, zc, (int)nitems, err);
+                                                           d.NX, d.NY, d.NZ, box.lo[0], box.lo[1], box.lo[2],
+                                                           box.hi[2], tiles_x, tiles_y, zc, (int)nitems, err);
   return cudaGetLastError();
 }
 

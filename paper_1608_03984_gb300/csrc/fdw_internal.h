@@ -230,7 +230,18 @@ cudaError_t closure_tc_net(ClosureNet *c, int storage, const void *u, const void
 // network on the FP16 inputs x16 into dst (FP32, dense [NZ][NY][NX])
 int closure_umma_reserve(ClosureNet *c);
 cudaError_t closure_umma_prepare(ClosureNet *c, cudaStream_t st);
-cudaError_t closure_umma_run(ClosureNet *c, const void *x16, float *dst, Dims d, int *err, cudaStream_t st);
+// Points whose network output the time loop uses: those at least
+// kClosureHalo points (the receptive-field radius of the three 3x3x3
+// layers) inside the physical grid; [lo, hi) per axis (x, y, z) on the
+// computational grid. The tensor-core kernels compute the output there
+// only (the points of a work item beyond hi are computed and unused).
+constexpr int kClosureHalo = 3;
+struct NetBox {
+  int lo[3], hi[3];
+  bool empty() const { return hi[0] <= lo[0] || hi[1] <= lo[1] || hi[2] <= lo[2]; }
+};
+cudaError_t closure_umma_run(ClosureNet *c, const void *x16, float *dst, Dims d, const NetBox &box, int *err,
+                             cudaStream_t st);
 
 }  // namespace fdw
 
