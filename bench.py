@@ -70,6 +70,8 @@ def parse():
     p.add_argument("--profile-closure-step", type=int, default=0, metavar="N",
                    help="only run 40 plain and 2 closure steps on an N^3 coarse grid (+20 sponge), "
                         "random network: the case the closure kernel is profiled on")
+    p.add_argument("--profile-closure-variant", type=int, default=0, choices=[0, 1, 2],
+                   help="inference kernels of --profile-closure-step: 0 tcgen05, 1 FP32, 2 mma.sync")
     return p.parse_args()
 
 
@@ -814,7 +816,7 @@ def run_e2e(args, orders, base, stream):
                     "%d steps, traces read back; wall clock" % nsteps}
 
 
-def profile_closure_step(n):
+def profile_closure_step(n, variant=0):
     """A small, fixed closure case for kernel profiling (not a measurement)."""
     import torch
     from paper_1608_03984_gb300 import closure as C, fdwave
@@ -823,6 +825,7 @@ def profile_closure_step(n):
     v_f, v_c, src = C.model(pr, 5064)
     cs = C.coarse_solver(pr, v_c, src, 100)
     net = fdwave.Closure()
+    net.set_variant(variant)
     net.set_params(C.init_params(0, last_scale=0.3))
     cs.step(40)
     cs.step_closure(net, 2)
@@ -835,7 +838,7 @@ def profile_closure_step(n):
 def main():
     args = parse()
     if args.profile_closure_step:
-        profile_closure_step(args.profile_closure_step)
+        profile_closure_step(args.profile_closure_step, args.profile_closure_variant)
         return
     orders = tuple(int(x) for x in args.orders.split(","))
     if args.impl == "reference":
