@@ -25,6 +25,40 @@ template <> __device__ __forceinline__ void atomic_add_st<__half>(__half *p, flo
 // Corner layout shared by sources and receivers: for point s and corner q,
 // ijk[(s*8+q)*3 + a] are the computational-grid indices (always inside the
 // grid; dropped corners have weight 0).
+// Forward injection of step n by the threads of one block.
+template <typename T>
+__device__ __forceinline__ void inject_step(const SparseLaunch &L, int n, size_t plane) {
+  for (int t = threadIdx.x; t < L.nsrc * 8; t += blockDim.x) {
+    const float wt = L.src_w[t];
+    if (wt == 0.f) continue;
+    const int s = t >> 3;
+    const int i = L.src_corner[t * 3 + 0], j = L.src_corner[t * 3 + 1], k = L.src_corner[t * 3 + 2];
+    const size_t p = (size_t)k * plane + (size_t)j * L.d.Xp + i;
+    const float amp = L.wavelet[(size_t)n * L.nsrc + s];
+    const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[k];
+    const float cc = St<T>::ld(((const T *)L.c)[p]);
+    const float v = cc * wt * (amp * L.amp_scale) * __frcp_rn(1.f + gh);
+    atomic_add_st<T>((T *)L.f0 + p, v);
+    if (L.f1) atomic_add_st<T>((T *)L.f1 + p, v);
+  }
+}
+
+// Receiver r's trace value of level n1.
+template <typename T>
+__device__ __forceinline__ void gather_receiver(const SparseLaunch &L, int r, int n1, size_t plane) {
+  const T *f = (const T *)L.f0;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int t = r * 8 + q;
+    const float wt = L.rec_w[t];
+    const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], k = L.rec_corner[t * 3 + 2];
+    const float v = St<T>::ld(f[(size_t)k * plane + (size_t)j * L.d.Xp + i]);
+    acc += (double)wt * (double)v;
+  }
+  L.traces[(size_t)n1 * L.nrec + r] = acc * L.trace_scale;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) inject_kernel(SparseLaunch L) {
   __shared__ int sn;
@@ -34,20 +68,7 @@ __global__ void __launch_bounds__(256) inject_kernel(SparseLaunch L) {
   if (threadIdx.x == 0) *L.step = L.adjoint ? n - 1 : n + 1;
   const size_t plane = L.d.plane();
   if (!L.adjoint) {
-    if (n < 0 || n >= L.nt_src) return;
-    for (int t = threadIdx.x; t < L.nsrc * 8; t += blockDim.x) {
-      const float wt = L.src_w[t];
-      if (wt == 0.f) continue;
-      const int s = t >> 3;
-      const int i = L.src_corner[t * 3 + 0], j = L.src_corner[t * 3 + 1], k = L.src_corner[t * 3 + 2];
-      const size_t p = (size_t)k * plane + (size_t)j * L.d.Xp + i;
-      const float amp = L.wavelet[(size_t)n * L.nsrc + s];
-      const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[k];
-      const float cc = St<T>::ld(((const T *)L.c)[p]);
-      const float v = cc * wt * (amp * L.amp_scale) * __frcp_rn(1.f + gh);
-      atomic_add_st<T>((T *)L.f0 + p, v);
-      if (L.f1) atomic_add_st<T>((T *)L.f1 + p, v);
-    }
+    if (n >= 0 && n < L.nt_src) inject_step<T>(L, n, plane);
   } else {
     // Adjoint step that produced level k = n - 1 (the residual was spread by
     // adjoint_spread_kernel just before). Source side of the adjoint:
@@ -76,18 +97,7 @@ __global__ void __launch_bounds__(256) gather_kernel(SparseLaunch L) {
   if (r >= L.nrec) return;
   const int n1 = *L.step;  // level just produced
   if (n1 < 0 || n1 > L.nt_rec) return;
-  const size_t plane = L.d.plane();
-  const T *f = (const T *)L.f0;
-  double acc = 0.0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int t = r * 8 + q;
-    const float wt = L.rec_w[t];
-    const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], k = L.rec_corner[t * 3 + 2];
-    const float v = St<T>::ld(f[(size_t)k * plane + (size_t)j * L.d.Xp + i]);
-    acc += (double)wt * (double)v;
-  }
-  L.traces[(size_t)n1 * L.nrec + r] = acc * L.trace_scale;
+  gather_receiver<T>(L, r, n1, L.d.plane());
 }
 
 // Adjoint step producing level k = *step - 1 (the counter is decremented by
@@ -125,36 +135,11 @@ __global__ void __launch_bounds__(256) inject_gather_kernel(SparseLaunch L) {
   const int n = sn;
   if (threadIdx.x == 0) *L.step = n + 1;
   const size_t plane = L.d.plane();
-  if (n >= 0 && n < L.nt_src) {
-    for (int t = threadIdx.x; t < L.nsrc * 8; t += blockDim.x) {
-      const float wt = L.src_w[t];
-      if (wt == 0.f) continue;
-      const int s = t >> 3;
-      const int i = L.src_corner[t * 3 + 0], j = L.src_corner[t * 3 + 1], k = L.src_corner[t * 3 + 2];
-      const size_t p = (size_t)k * plane + (size_t)j * L.d.Xp + i;
-      const float amp = L.wavelet[(size_t)n * L.nsrc + s];
-      const float gh = L.sp.gx[i] + L.sp.gy[j] + L.sp.gz[k];
-      const float cc = St<T>::ld(((const T *)L.c)[p]);
-      const float v = cc * wt * (amp * L.amp_scale) * __frcp_rn(1.f + gh);
-      atomic_add_st<T>((T *)L.f0 + p, v);
-      if (L.f1) atomic_add_st<T>((T *)L.f1 + p, v);
-    }
-  }
+  if (n >= 0 && n < L.nt_src) inject_step<T>(L, n, plane);
   __syncthreads();
   const int n1 = n + 1;  // level just produced
   const int r = threadIdx.x;
-  if (r >= L.nrec || n1 < 0 || n1 > L.nt_rec) return;
-  const T *f = (const T *)L.f0;
-  double acc = 0.0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const int t = r * 8 + q;
-    const float wt = L.rec_w[t];
-    const int i = L.rec_corner[t * 3 + 0], j = L.rec_corner[t * 3 + 1], k = L.rec_corner[t * 3 + 2];
-    const float v = St<T>::ld(f[(size_t)k * plane + (size_t)j * L.d.Xp + i]);
-    acc += (double)wt * (double)v;
-  }
-  L.traces[(size_t)n1 * L.nrec + r] = acc * L.trace_scale;
+  if (r < L.nrec && n1 >= 0 && n1 <= L.nt_rec) gather_receiver<T>(L, r, n1, plane);
 }
 
 template <typename T>
