@@ -55,6 +55,22 @@ def test_closure_operating_point():
     assert bench.operating_point(0.0100, ms, bad)["every"] == 1
 
 
+def test_closure_operating_point_chosen_on_validation_models():
+    """With validation errors, k is chosen on them and the evaluation
+    models' error and speed-up at that k are reported."""
+    ms = {"fine": 1000.0, "closure": 1000.0}
+    sub = {"2": {"error_vs_fine": {"field": 0.0101}, "speedup_vs_fine": 1.9},
+           "4": {"error_vs_fine": {"field": 0.0104}, "speedup_vs_fine": 3.4},
+           "8": {"error_vs_fine": {"field": 0.0300}, "speedup_vs_fine": 5.6}}
+    val = {"closure": 0.020, "every": {"2": 0.0201, "4": 0.0250, "8": 0.0600}, "label": "validation models 1, 2"}
+    op = bench.operating_point(0.0100, ms, sub, val)
+    assert op == {"every": 2, "field_error": 0.0101, "speedup_vs_fine": 1.9,
+                  "selected_on": "validation models 1, 2"}
+    val["every"] = {"2": 0.03, "4": 0.04, "8": 0.05}
+    op = bench.operating_point(0.0100, ms, sub, val)
+    assert op["every"] == 1 and op["field_error"] == 0.0100 and op["speedup_vs_fine"] == 1.0
+
+
 def _full_result():
     """A result of the shape run_fdwave assembles, with every section filled
     as on the benchmark (16 held-out closure models, five orders)."""
