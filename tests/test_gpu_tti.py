@@ -163,7 +163,7 @@ def test_every_tti_configuration(fdw, O, order, tile):
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
-@pytest.mark.parametrize("order", [2, 4, 8])
+@pytest.mark.parametrize("order", [2, 4, 6, 8])
 def test_row_pair_kernel_same_bits(fdw, order, storage):
     """Two rows per thread and the z unrolling change which thread computes
     a point and when, not its arithmetic: the field-pair configurations give
@@ -171,7 +171,7 @@ def test_row_pair_kernel_same_bits(fdw, order, storage):
     source)."""
     w = small_tti(n=(29, 19, 41), order=order, nt=6, seed=90 + order)
     out = {}
-    same = ((7, 12), (8, 10), (7, 8))
+    same = ((7, 12), (8, 10), (7, 8), (7, 9))
     for tile in sorted({t for p in same for t in p}):
         s = tti_solver(fdw, w, storage=storage)
         s.set_tile_config(tile)
