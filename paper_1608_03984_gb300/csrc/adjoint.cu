@@ -17,7 +17,9 @@ namespace fdw {
 
 // One block per row (j, k) of the padded layout, threads along x: the
 // damping of the row is loaded once and no 64-bit division is done per
-// point (that index arithmetic made this per-step kernel issue-bound).
+// point (that index arithmetic made this per-step kernel issue-bound). Used
+// for grids of 2^31 or more groups of four points; grad_accum4_kernel below
+// otherwise.
 template <typename T>
 __global__ void grad_accum_kernel(const T *__restrict__ mu, const T *__restrict__ u1,
                                   const T *__restrict__ u0, const T *__restrict__ um1,
@@ -35,6 +37,41 @@ __global__ void grad_accum_kernel(const T *__restrict__ mu, const T *__restrict_
                       (um1 ? (1.f - gh) * St<T>::ld(um1[p]) : 0.f);
       g32[p] = fmaf(a, b, g32[p]);
     }
+  }
+}
+
+// The same term four points at a time (the padded row length is a multiple
+// of 32): 16-byte loads of the fields and of the FP32 partial sum, one 32-bit
+// division per four points for the row index. Points of the row padding
+// (x >= NX) are skipped.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    grad_accum4_kernel(const T *__restrict__ mu, const T *__restrict__ u1, const T *__restrict__ u0,
+                       const T *__restrict__ um1, float *__restrict__ g32, Dims d, Sponge sp, int nq) {
+  using V = struct alignas(4 * sizeof(T)) { T v[4]; };
+  const int xq = d.Xp / 4;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const int row = q / xq, i0 = (q - row * xq) * 4;
+    if (i0 >= d.NX) continue;
+    const int j = row % d.NY, k = row / d.NY;
+    const float gyz = sp.gy[j] + sp.gz[k];
+    const V a = reinterpret_cast<const V *>(mu)[q];
+    const V b1 = reinterpret_cast<const V *>(u1)[q];
+    const V b0 = reinterpret_cast<const V *>(u0)[q];
+    V bm;
+    if (um1) bm = reinterpret_cast<const V *>(um1)[q];
+    float4 g = reinterpret_cast<float4 *>(g32)[q];
+    float *ge = reinterpret_cast<float *>(&g);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (i0 + e < d.NX) {
+        const float gh = sp.gx[i0 + e] + gyz;
+        const float b = (1.f + gh) * St<T>::ld(b1.v[e]) - 2.f * St<T>::ld(b0.v[e]) +
+                        (um1 ? (1.f - gh) * St<T>::ld(bm.v[e]) : 0.f);
+        ge[e] = fmaf(St<T>::ld(a.v[e]), b, ge[e]);
+      }
+    }
+    reinterpret_cast<float4 *>(g32)[q] = g;
   }
 }
 
@@ -79,6 +116,28 @@ static int row_grid(const Dims &d) {
 
 cudaError_t launch_grad_accum(int storage, const void *mu, const void *u1, const void *u0,
                               const void *um1, float *g32, Dims d, Sponge sp, cudaStream_t st) {
+  const size_t nq = d.vol() / 4;
+  if (d.Xp % 4 == 0 && nq < 0x7fffffffull) {
+    const int blocks = grid_for(nq);
+    switch (storage) {
+      case FDW_F32:
+        grad_accum4_kernel<float><<<blocks, 256, 0, st>>>((const float *)mu, (const float *)u1, (const float *)u0,
+                                                          (const float *)um1, g32, d, sp, (int)nq);
+        break;
+      case FDW_BF16:
+        grad_accum4_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+            (const __nv_bfloat16 *)mu, (const __nv_bfloat16 *)u1, (const __nv_bfloat16 *)u0,
+            (const __nv_bfloat16 *)um1, g32, d, sp, (int)nq);
+        break;
+      case FDW_F16:
+        grad_accum4_kernel<__half><<<blocks, 256, 0, st>>>((const __half *)mu, (const __half *)u1,
+                                                           (const __half *)u0, (const __half *)um1, g32, d, sp,
+                                                           (int)nq);
+        break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   switch (storage) {
     case FDW_F32:
       grad_accum_kernel<float><<<row_grid(d), 256, 0, st>>>(
