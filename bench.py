@@ -461,7 +461,7 @@ def run_tti(args, stream, steps, warmup):
     random eps/delta/theta/phi, orders 8 and 12, FP32 / BF16 / FP16 storage
     (FP32 arithmetic). Kernel time from CUDA events around each launch."""
     import torch
-    from paper_1608_03984_gb300 import fdwave, synth
+    from paper_1608_03984_gb300 import fdwave, opmodel, synth
     hbm, _ = peaks()
     w = synth.random_tti(n=args.tti_n, nb=args.nb, order=8, nt=steps + warmup + 2, nrec_side=128)
     out = {"workload": "random_tti %d^3 + %d-point sponge (%d^3), h=12.5 m, orders 8/12"
@@ -484,9 +484,18 @@ def run_tti(args, stream, steps, warmup):
             avg = ms / max(n, 1)
             gpts = w.points / (avg / 1e3) / 1e9
             bpp = (4 if st == "f32" else 2) * TTI_FIELD_BYTES
+            # the paper's model of this kernel (Table 1, Eq. eqn_oi and
+            # Eq. perf-limits: 15 fields in the storage's word, F(k) FLOP per
+            # point) with the measured HBM bandwidth and the FP32 peak at the
+            # maximum SM clock: the roof the paper would predict
+            k = order + 1
+            word = 4 if st == "f32" else 2
+            model_roof = opmodel.roofline(opmodel.oi("tti", k, word), hbm, opmodel.fp32_peak_gflops()) / \
+                opmodel.flops_per_point("tti", k)
             out.setdefault(str(order), {})[st] = {
                 "kernel_ms": avg, "gpts": gpts, "achieved_gbs": gpts * bpp,
-                "frac_of_measured_hbm": gpts * bpp / hbm}
+                "frac_of_measured_hbm": gpts * bpp / hbm,
+                "paper_model_roof_gpts": model_roof, "frac_of_paper_model_roof": gpts / model_roof}
     return out
 
 
@@ -741,7 +750,8 @@ def headline(full, details_path):
     summ = {}
     tti = full.get("tti")
     if tti:
-        summ["tti"] = {o: {st: {"gpts": _r(v["gpts"]), "frac": _r(v["frac_of_measured_hbm"])}
+        summ["tti"] = {o: {st: {"gpts": _r(v["gpts"]), "frac": _r(v["frac_of_measured_hbm"]),
+                                "frac_model": _r(v.get("frac_of_paper_model_roof"), 3)}
                            for st, v in tti[o].items()} for o in tti if o.isdigit()}
     st = full.get("storage")
     if st:
