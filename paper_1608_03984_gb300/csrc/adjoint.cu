@@ -75,6 +75,46 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Two consecutive terms in one pass, four points at a time: term j-1,
+// mu_j (P u_j - 2 u_{j-1} + Q u_{j-2}), then term j-2, mu_{j-1} (P u_{j-1}
+// - 2 u_{j-2} + Q u_{j-3}) (u_{j-3} = 0 when absent), added in that order
+// as the single-term kernel would over two steps; the partial sum and the
+// shared levels are read once instead of twice.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    grad_accum4_pair_kernel(const T *__restrict__ mu_a, const T *__restrict__ mu_b, const T *__restrict__ ua,
+                            const T *__restrict__ ub, const T *__restrict__ uc, const T *__restrict__ ud,
+                            float *__restrict__ g32, Dims d, Sponge sp, int nq) {
+  using V = struct alignas(4 * sizeof(T)) { T v[4]; };
+  const int xq = d.Xp / 4;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const int row = q / xq, i0 = (q - row * xq) * 4;
+    if (i0 >= d.NX) continue;
+    const int j = row % d.NY, k = row / d.NY;
+    const float gyz = sp.gy[j] + sp.gz[k];
+    const V ma = reinterpret_cast<const V *>(mu_a)[q];
+    const V mb = reinterpret_cast<const V *>(mu_b)[q];
+    const V a = reinterpret_cast<const V *>(ua)[q];
+    const V b = reinterpret_cast<const V *>(ub)[q];
+    const V c = reinterpret_cast<const V *>(uc)[q];
+    V dd;
+    if (ud) dd = reinterpret_cast<const V *>(ud)[q];
+    float4 g = reinterpret_cast<float4 *>(g32)[q];
+    float *ge = reinterpret_cast<float *>(&g);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      if (i0 + e < d.NX) {
+        const float gh = sp.gx[i0 + e] + gyz;
+        const float t1 = (1.f + gh) * St<T>::ld(a.v[e]) - 2.f * St<T>::ld(b.v[e]) + (1.f - gh) * St<T>::ld(c.v[e]);
+        const float t2 = (1.f + gh) * St<T>::ld(b.v[e]) - 2.f * St<T>::ld(c.v[e]) +
+                         (ud ? (1.f - gh) * St<T>::ld(dd.v[e]) : 0.f);
+        ge[e] = fmaf(St<T>::ld(mb.v[e]), t2, fmaf(St<T>::ld(ma.v[e]), t1, ge[e]));
+      }
+    }
+    reinterpret_cast<float4 *>(g32)[q] = g;
+  }
+}
+
 __global__ void grad_flush_kernel(float *__restrict__ g32, double *__restrict__ g64, size_t n) {
   for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < n;
        p += (size_t)gridDim.x * blockDim.x) {
@@ -151,6 +191,36 @@ cudaError_t launch_grad_accum(int storage, const void *mu, const void *u1, const
     case FDW_F16:
       grad_accum_kernel<__half><<<row_grid(d), 256, 0, st>>>(
           (const __half *)mu, (const __half *)u1, (const __half *)u0, (const __half *)um1, g32, d, sp);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_accum_pair(int storage, const void *mu_a, const void *mu_b, const void *ua,
+                                   const void *ub, const void *uc, const void *ud, float *g32, Dims d, Sponge sp,
+                                   cudaStream_t st) {
+  const size_t nq = d.vol() / 4;
+  if (d.Xp % 4 != 0 || nq >= 0x7fffffffull) {  // two single terms
+    cudaError_t e = launch_grad_accum(storage, mu_a, ua, ub, uc, g32, d, sp, st);
+    return e != cudaSuccess ? e : launch_grad_accum(storage, mu_b, ub, uc, ud, g32, d, sp, st);
+  }
+  const int blocks = grid_for(nq);
+  switch (storage) {
+    case FDW_F32:
+      grad_accum4_pair_kernel<float><<<blocks, 256, 0, st>>>(
+          (const float *)mu_a, (const float *)mu_b, (const float *)ua, (const float *)ub, (const float *)uc,
+          (const float *)ud, g32, d, sp, (int)nq);
+      break;
+    case FDW_BF16:
+      grad_accum4_pair_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(
+          (const __nv_bfloat16 *)mu_a, (const __nv_bfloat16 *)mu_b, (const __nv_bfloat16 *)ua,
+          (const __nv_bfloat16 *)ub, (const __nv_bfloat16 *)uc, (const __nv_bfloat16 *)ud, g32, d, sp, (int)nq);
+      break;
+    case FDW_F16:
+      grad_accum4_pair_kernel<__half><<<blocks, 256, 0, st>>>(
+          (const __half *)mu_a, (const __half *)mu_b, (const __half *)ua, (const __half *)ub, (const __half *)uc,
+          (const __half *)ud, g32, d, sp, (int)nq);
       break;
     default: return cudaErrorInvalidValue;
   }

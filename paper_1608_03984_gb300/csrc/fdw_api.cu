@@ -1045,6 +1045,11 @@ extern "C" int fdw_adjoint_step(fdw_solver *s, int nsteps) {
   DeviceGuard g(s->device);
   int rc = acoustic_prepare(s->storage, s->r, s->tile) == cudaSuccess ? FDW_OK : FDW_ERR_CUDA;
   if (rc) return fail(rc, "kernel attribute");
+  // A gradient term is held back one step when the next step of this call
+  // has one too: the two are added in one pass (both adjoint levels are
+  // still in the ping-pong buffers then; the history ring may be refilled
+  // after the call, so nothing is held across calls).
+  int held = -1;  // level j of the held term j - 1
   for (int n = 0; n < nsteps; ++n) {
     const int cur = s->acur, nxt = 1 - cur;
     const int j = s->ak - 1;  // level produced: mu_j
@@ -1094,9 +1099,23 @@ extern "C" int fdw_adjoint_step(fdw_solver *s, int nsteps) {
       const int s1 = hist_slot(s, j), s0 = hist_slot(s, j - 1), sm = hist_slot(s, j - 2);
       if (s1 < 0 || s0 < 0 || (sm < 0 && j - 2 >= 0))
         return fail(FDW_ERR_STATE, "forward levels %d..%d are not in the history", j - 2, j);
-      CK(launch_grad_accum(s->storage, s->a[nxt], s->hist[s1], s->hist[s0],
-                           sm >= 0 ? s->hist[sm] : nullptr, s->grad32, s->d, L.sp, s->stream));
-      if (++s->grad_pending >= 64) {
+      int added = 0;
+      if (held >= 0) {
+        // terms held - 1 = j and j - 1: mu_{j+1} (now in a[cur]) and mu_j
+        const int sh = hist_slot(s, held);
+        if (sh < 0) return fail(FDW_ERR_STATE, "forward level %d is not in the history", held);
+        CK(launch_grad_accum_pair(s->storage, s->a[cur], s->a[nxt], s->hist[sh], s->hist[s1], s->hist[s0],
+                                  sm >= 0 ? s->hist[sm] : nullptr, s->grad32, s->d, L.sp, s->stream));
+        held = -1;
+        added = 2;
+      } else if (n + 1 < nsteps && j >= 2 && s->grad_pending + 2 <= 64) {
+        held = j;  // the next step's term j - 2 joins it
+      } else {
+        CK(launch_grad_accum(s->storage, s->a[nxt], s->hist[s1], s->hist[s0],
+                             sm >= 0 ? s->hist[sm] : nullptr, s->grad32, s->d, L.sp, s->stream));
+        added = 1;
+      }
+      if ((s->grad_pending += added) >= 64) {
         CK(launch_grad_flush(s->grad32, s->grad64, s->d.vol(), s->stream));
         s->grad_pending = 0;
       }

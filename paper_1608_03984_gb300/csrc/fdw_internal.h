@@ -253,6 +253,11 @@ namespace fdw {
 // FWI gradient kernels (adjoint.cu)
 cudaError_t launch_grad_accum(int storage, const void *mu, const void *u1, const void *u0,
                               const void *um1, float *g32, Dims d, Sponge sp, cudaStream_t st);
+// Terms j-1 and j-2 in one pass: mu_a = mu_j, mu_b = mu_{j-1}, ua..ud =
+// u_j, u_{j-1}, u_{j-2}, u_{j-3} (ud may be null: u_{j-3} = 0).
+cudaError_t launch_grad_accum_pair(int storage, const void *mu_a, const void *mu_b, const void *ua,
+                                   const void *ub, const void *uc, const void *ud, float *g32, Dims d, Sponge sp,
+                                   cudaStream_t st);
 cudaError_t launch_grad_flush(float *g32, double *g64, size_t n, cudaStream_t st);
 cudaError_t launch_grad_physical(const double *g64, Dims d, int nx, int ny, int nz, int nb,
                                  double scale, double *out, cudaStream_t st);
