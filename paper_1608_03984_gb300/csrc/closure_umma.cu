@@ -2,9 +2,10 @@
 // tensor cores (tcgen05.mma, accumulators in tensor memory).
 //
 // The network (closure.cu: three 3x3x3 convolutions 3 -> 16 -> 16 -> 1,
-// ReLU between, zero padding at every layer) runs over a whole grid in one
-// persistent kernel: each CTA takes work items (an output column of
-// TXO x TYO points and a chunk of z planes) and marches the planes through
+// ReLU between, zero padding at the faces of the grid) runs over the box of
+// points the time loop corrects, in one persistent kernel: each CTA takes
+// work items (an output column of TXO x TYO points and a chunk of z planes,
+// tiling the box) and marches the planes through
 // a pipeline whose three convolutions are implicit GEMMs with
 //   M = 128 points (an 8 x 16 block of one plane; the 8-row core matrices
 //       of the operand are 8 consecutive x points, stepped by the row
